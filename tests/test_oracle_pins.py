@@ -1,0 +1,462 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks an oracle function against something that is not the oracle itself:
+textbook values, closed forms, values the paper states, a library routine on a special
+case, brute force on tiny inputs, or an invariant of the method.
+"""
+import os
+from math import comb, sqrt
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.special import eval_legendre
+
+from oracle import fock, mpo as M, mps as S, quadrature as Q
+from paper_1703_04789_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    return np.loadtxt(os.path.join(GOLDEN, name), comments="#")
+
+
+# ---- quadrature (Eq. pmpo, Eq. exactQuadrature) ------------------------------------------
+
+def test_gauss_legendre_textbook_values():
+    ref = _load("gauss_legendre_5.txt")
+    x, w = Q.gauss_legendre(5)
+    assert np.allclose(x, ref[:, 0], atol=1e-10)
+    assert np.allclose(w, ref[:, 1], atol=1e-10)
+    # 3-point closed form: nodes 0, +-sqrt(3/5), weights 8/9, 5/9
+    x3, w3 = Q.gauss_legendre(3)
+    assert np.allclose(x3, [-sqrt(0.6), 0.0, sqrt(0.6)], atol=1e-15)
+    assert np.allclose(w3, [5 / 9, 8 / 9, 5 / 9], atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 8, 12])
+def test_gauss_legendre_exact_degree(n):
+    x, w = Q.gauss_legendre(n)
+    for k in range(2 * n):
+        exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+        assert abs(np.dot(w, x ** k) - exact) < 1e-13
+    k = 2 * n
+    assert abs(np.dot(w, x ** k) - 2.0 / (k + 1)) > 1e-9  # degree 2n is not integrated exactly
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.3, 1.1, 2.0, np.pi])
+def test_wigner_d_closed_forms(beta):
+    d = Q.wigner_small_d
+    assert abs(d(1, 1, 1, beta) - np.cos(beta / 2)) < 1e-14
+    assert abs(d(1, -1, -1, beta) - np.cos(beta / 2)) < 1e-14
+    assert abs(d(1, 1, -1, beta) + np.sin(beta / 2)) < 1e-14
+    assert abs(d(2, 0, 0, beta) - np.cos(beta)) < 1e-14
+    assert abs(d(2, 2, 2, beta) - (1 + np.cos(beta)) / 2) < 1e-14
+    assert abs(d(2, 2, 0, beta) + np.sin(beta) / sqrt(2)) < 1e-14
+    for two_j in range(0, 12, 2):
+        assert abs(d(two_j, 0, 0, beta) - eval_legendre(two_j // 2, np.cos(beta))) < 1e-12
+
+
+@pytest.mark.parametrize("two_j", [1, 2, 3, 4, 7])
+def test_wigner_d_orthogonal_rows(two_j):
+    beta = 0.77
+    ms = range(-two_j, two_j + 1, 2)
+    Dm = np.array([[Q.wigner_small_d(two_j, a, b, beta) for b in ms] for a in ms])
+    assert np.allclose(Dm @ Dm.T, np.eye(len(ms)), atol=1e-13)
+    assert np.allclose(np.array([[Q.wigner_small_d(two_j, a, b, 0.0) for b in ms] for a in ms]), np.eye(len(ms)))
+
+
+def test_exact_quadrature_rule_values():
+    for K, N, twoM, twoS, ng in _load("exact_quadrature.txt").astype(int):
+        assert Q.n_exact(K, N, twoM, twoS) == ng, (K, N, twoM, twoS)
+
+
+@pytest.mark.parametrize("twoM", [0, 2])
+def test_discrete_orthogonality_of_d(twoM):
+    """With n points, sum_g (2S+1)/2 w_g d^S_MM d^S'_MM = delta_SS' whenever the product is a
+    polynomial in cos(beta) of degree <= 2n-1 (both have degree <= S)."""
+    n = 5
+    x, w = Q.gauss_legendre(n)
+    beta = np.arccos(x)
+    Ss = [s for s in range(abs(twoM), 12, 2) if (s + s) // 2 <= 2 * n - 1]
+    for a in Ss:
+        for b in Ss:
+            if (a + b) // 2 > 2 * n - 1:
+                continue
+            val = 0.5 * (a + 1) * sum(wg * Q.wigner_small_d(a, twoM, twoM, bg) * Q.wigner_small_d(b, twoM, twoM, bg)
+                                      for wg, bg in zip(w, beta))
+            assert abs(val - (1.0 if a == b else 0.0)) < 1e-12, (a, b)
+
+
+# ---- rotations (Eq. expSy) ----------------------------------------------------------------
+
+def test_site_rotation_is_exponential_of_local_sy():
+    gen = -0.5 * (M.S_PLUS - M.S_MINUS)  # -i S_y, real
+    for b in (0.1, 1.3, 2.9):
+        assert np.allclose(Q.site_rotation(b), sla.expm(b * gen), atol=1e-14)
+
+
+@pytest.mark.parametrize("K,N", [(2, 2), (3, 3), (3, 4)])
+def test_product_of_site_rotations_is_many_body_rotation(K, N):
+    G, basis = fock.total_sy_generator(K, N)
+    beta = 0.9
+    R = sla.expm(beta * G.toarray())
+    idx = fock.mask_to_sites(basis, K)
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(len(basis))
+    full = np.zeros(4 ** K)
+    full[idx] = v
+    out = fock.apply_site_ops(full, [Q.site_rotation(beta)] * K)
+    assert np.allclose(out[idx], R @ v, atol=1e-13)
+    assert np.allclose(np.delete(out, idx), 0.0, atol=1e-14)  # rotation keeps N
+
+
+# ---- exact diagonalisation (Eq. sqH) -------------------------------------------------------
+
+def test_hubbard_dimer_closed_form():
+    for U in (0.0, 1.0, 4.0, 8.0):
+        h1, eri = inputs.hubbard_chain(2, 1.0, U)
+        e, _, _ = fock.lowest_spin_state(2, 1, 1, h1, eri, 0)
+        assert abs(e - (U - sqrt(U * U + 16.0)) / 2) < 1e-12
+        et, _, _ = fock.lowest_spin_state(2, 2, 0, h1, eri, 2)
+        assert abs(et) < 1e-12
+
+
+@pytest.mark.parametrize("L,twoS", [(8, 0), (8, 2), (24, 0), (24, 2)])
+def test_free_chain_single_particle_sum(L, twoS):
+    """U = 0 open chain: E = sum of occupied levels -2t cos(pi j/(L+1)); checked on ED for L=8
+    and on the closed form's known values for L=24 (no ED)."""
+    levels = np.sort(-2.0 * np.cos(np.pi * np.arange(1, L + 1) / (L + 1)))
+    Na, Nb = (L + twoS) // 2, (L - twoS) // 2
+    e_cf = levels[:Na].sum() + levels[:Nb].sum()
+    known = {(8, 0): -9.5175409663, (8, 2): -8.8229482556, (24, 0): -29.8519422198, (24, 2): -29.6007801417}
+    assert abs(e_cf - known[(L, twoS)]) < 1e-9
+    if L <= 8:
+        h1, eri = inputs.hubbard_chain(L, 1.0, 0.0)
+        e, _, _ = fock.lowest_spin_state(L, Na, Nb, h1, None, twoS)
+        assert abs(e - e_cf) < 1e-9
+
+
+def test_random_one_body_ground_state_is_orbital_sum():
+    """General (non-nearest-neighbour) h1 exercises every Jordan-Wigner string."""
+    K = 5
+    rng = np.random.default_rng(7)
+    h1 = rng.standard_normal((K, K))
+    h1 = h1 + h1.T
+    eps = np.linalg.eigvalsh(h1)
+    for Na, Nb in ((2, 2), (3, 1), (3, 2)):
+        H, _ = fock.hamiltonian(K, Na, Nb, h1, None)
+        e = np.linalg.eigvalsh(H.toarray())[0]
+        assert abs(e - eps[:Na].sum() - eps[:Nb].sum()) < 1e-10
+
+
+def test_two_body_slater_condon_diagonal():
+    """<D|H|D> = sum_i h_ii + 1/2 sum_ij [(ii|jj) - delta_{s_i s_j} (ij|ji)] for every
+    determinant D (fixes the sign of exchange and the 1/2)."""
+    K = 4
+    h1, eri, _ = inputs.synthetic_active_space(K, 11)
+    H, basis = fock.hamiltonian(K, 2, 1, h1, eri)
+    Hd = H.diagonal()
+    for j, m in enumerate(basis):
+        occ = [(p // 2, p % 2) for p in range(2 * K) if (int(m) >> p) & 1]
+        e = sum(h1[k, k] for k, _ in occ)
+        for (k, s) in occ:
+            for (l, t) in occ:
+                e += 0.5 * eri[k, k, l, l]
+                if s == t:
+                    e -= 0.5 * eri[k, l, l, k]
+        assert abs(Hd[j] - e) < 1e-12
+
+
+def test_hamiltonian_is_spin_free():
+    K = 4
+    h1, eri, _ = inputs.synthetic_active_space(K, 3)
+    H, _ = fock.hamiltonian(K, 2, 2, h1, eri)
+    S2 = fock.s_squared(K, 2, 2)
+    assert abs(H - H.T).max() < 1e-13
+    assert abs(H @ S2 - S2 @ H).max() < 1e-12
+
+
+def test_atomic_limit():
+    """t = 0: the lowest S=0 energy at half filling is 0 (no double occupancy), with two
+    extra electrons it is 2U."""
+    h1, eri = inputs.hubbard_chain(4, 0.0, 3.0)
+    e, _, _ = fock.lowest_spin_state(4, 2, 2, h1, eri, 0)
+    assert abs(e) < 1e-12
+    e, _, _ = fock.lowest_spin_state(4, 3, 3, h1, eri, 0)
+    assert abs(e - 6.0) < 1e-12
+
+
+# ---- MPOs (Eq. Wfac merged to spatial sites, Eq. Sfac) -------------------------------------
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_hubbard_mpo_equals_ed(L):
+    h1, eri = inputs.hubbard_chain(L, 1.3, 2.7)
+    Hd = M.mpo_to_dense(M.hubbard_mpo(L, 1.3, 2.7))
+    for Na in range(L + 1):
+        for Nb in range(L + 1):
+            H, basis = fock.hamiltonian(L, Na, Nb, h1, eri)
+            idx = fock.mask_to_sites(basis, L)
+            assert np.allclose(Hd[np.ix_(idx, idx)], H.toarray(), atol=1e-13)
+
+
+@pytest.mark.parametrize("K", [2, 3, 4])
+def test_s2_mpo_equals_ed(K):
+    S2d = M.mpo_to_dense(M.s2_mpo(K))
+    for Na in range(K + 1):
+        for Nb in range(K + 1):
+            basis = fock.sector_basis(K, Na, Nb)
+            idx = fock.mask_to_sites(basis, K)
+            assert np.allclose(S2d[np.ix_(idx, idx)], fock.s_squared(K, Na, Nb).toarray(), atol=1e-13)
+
+
+# ---- the projector (Eq. PSMM, Eq. pmpo) ----------------------------------------------------
+
+def _projector_matrix(K, N, twoM, twoS, n_beta):
+    Na, Nb = inputs.electron_counts(N, twoM)
+    basis = fock.sector_basis(K, Na, Nb)
+    idx = fock.mask_to_sites(basis, K)
+    beta, c = Q.projector_quadrature(twoS, twoM, n_beta)
+    P = np.zeros((len(basis), len(basis)))
+    for j in range(len(basis)):
+        full = np.zeros(4 ** K)
+        full[idx[j]] = 1.0
+        acc = sum(cg * fock.apply_site_ops(full, [Q.site_rotation(b)] * K) for b, cg in zip(beta, c))
+        P[:, j] = acc[idx]
+    return P, basis
+
+
+@pytest.mark.parametrize("K,N,twoM,twoS", [(4, 4, 0, 0), (4, 4, 0, 2), (5, 5, 1, 1), (5, 5, 1, 3), (4, 4, 2, 2)])
+def test_projector_idempotent_symmetric_and_counts_multiplets(K, N, twoM, twoS):
+    ng = Q.n_exact(K, N, twoM, twoS)
+    P, basis = _projector_matrix(K, N, twoM, twoS, ng)
+    assert np.allclose(P, P.T, atol=1e-13)
+    assert np.allclose(P @ P, P, atol=1e-12)
+    Na, Nb = inputs.electron_counts(N, twoM)
+    Ms = (N + twoS) // 2
+    dimS = comb(K, Ms) * comb(K, N - Ms)
+    dimS1 = comb(K, Ms + 1) * comb(K, N - Ms - 1) if N - Ms - 1 >= 0 else 0
+    assert abs(np.trace(P) - (dimS - dimS1)) < 1e-10
+    S2 = fock.s_squared(K, Na, Nb).toarray()
+    s = 0.5 * twoS
+    assert np.allclose(S2 @ P, s * (s + 1) * P, atol=1e-11)
+
+
+def test_projector_with_too_few_points_is_not_idempotent():
+    K, N, twoM, twoS = 4, 4, 0, 0
+    ng = Q.n_exact(K, N, twoM, twoS)
+    P, _ = _projector_matrix(K, N, twoM, twoS, ng - 1)
+    assert np.abs(P @ P - P).max() > 1e-3
+
+
+def test_singlet_count_for_eight_site_half_filling():
+    # 4900 states with Sz = 0, 3136 with Sz = 1: 1764 singlets
+    assert comb(8, 4) ** 2 - comb(8, 5) * comb(8, 3) == 1764
+
+
+# ---- the projected action against brute force (Eq. geproblem, Fig. spmpsOpt) ---------------
+
+def _embedding(mps, k):
+    """Columns: full 4^K vectors of the two-site basis |a> |s1> |s2> |b> at (k, k+1),
+    built from the MPS tensors alone."""
+    K = mps.K
+    left = np.ones((1, 1))
+    for i in range(k):
+        left = np.einsum("Xa,asb->Xsb", left, mps.A[i]).reshape(-1, mps.A[i].shape[2])
+    right = np.ones((1, 1))
+    for i in range(K - 1, k + 1, -1):
+        right = np.einsum("asb,bY->asY", mps.A[i], right).reshape(mps.A[i].shape[0], -1)
+    Dl, Dr = left.shape[1], right.shape[0]
+    cols = []
+    for a in range(Dl):
+        for s1 in range(4):
+            for s2 in range(4):
+                for b in range(Dr):
+                    e1 = np.zeros(4); e1[s1] = 1
+                    e2 = np.zeros(4); e2[s2] = 1
+                    cols.append(np.kron(np.kron(np.kron(left[:, a], e1), e2), right[b]))
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("K,N,twoM,twoS,D,seed", [(4, 4, 0, 0, 8, 1), (5, 5, 1, 1, 6, 2), (4, 4, 0, 2, 8, 3), (5, 4, 0, 0, 7, 4)])
+def test_projected_apply_matches_brute_force(K, N, twoM, twoS, D, seed):
+    U, t = 3.0, 1.0
+    h1, eri = inputs.hubbard_chain(K, t, U)
+    labels, tens = inputs.random_mps(K, N, twoM, D, seed)
+    ng = Q.n_exact(K, N, twoM, twoS)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, t, U), twoS, twoM, ng)
+    # move the centre to sites (k, k+1) by left-canonical steps through the oracle itself,
+    # then compare against brute force built from the MPS tensors only
+    Na, Nb = inputs.electron_counts(N, twoM)
+    H, basis = fock.hamiltonian(K, Na, Nb, h1, eri)
+    idx = fock.mask_to_sites(basis, K)
+    beta, c = Q.projector_quadrature(twoS, twoM, ng)
+    rng = np.random.default_rng(seed + 100)
+    for k in range(K - 1):
+        V = _embedding(P.mps, k)
+        ql, qr = P.mps.labels[k], P.mps.labels[k + 2]
+        mask = S.two_site_mask(ql, qr)
+        x = np.where(mask, rng.standard_normal(mask.shape), 0.0)
+        y, z = P.apply(x, k)
+        full = V @ x.reshape(-1)
+        proj = sum(cg * fock.apply_site_ops(full, [Q.site_rotation(b)] * K) for b, cg in zip(beta, c))
+        sec = proj[idx]
+        hy = np.zeros(4 ** K); hy[idx] = H @ sec
+        nz = np.zeros(4 ** K); nz[idx] = sec
+        y_bf = (V.T @ hy).reshape(x.shape) * mask
+        z_bf = (V.T @ nz).reshape(x.shape) * mask
+        assert np.abs(y - y_bf).max() < 1e-12 * max(1.0, np.abs(y_bf).max())
+        assert np.abs(z - z_bf).max() < 1e-12 * max(1.0, np.abs(z_bf).max())
+        if k < K - 2:
+            S.two_site_step(P, k, True, D, S.SweepLog(), max_iter=3)
+
+
+def test_heff_neff_symmetric_and_metric_in_unit_interval():
+    K, N, twoM, twoS, D = 5, 5, 1, 1, 8
+    labels, tens = inputs.random_mps(K, N, twoM, D, 5)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, Q.n_exact(K, N, twoM, twoS))
+    k = 0
+    mask = S.two_site_mask(P.mps.labels[k], P.mps.labels[k + 2])
+    sel = np.nonzero(mask.reshape(-1))[0]
+    Hm = np.zeros((len(sel), len(sel)))
+    Nm = np.zeros_like(Hm)
+    for j, p in enumerate(sel):
+        e = np.zeros(mask.size); e[p] = 1.0
+        y, z = P.apply(e.reshape(mask.shape), k)
+        Hm[:, j] = y.reshape(-1)[sel]
+        Nm[:, j] = z.reshape(-1)[sel]
+    assert np.allclose(Hm, Hm.T, atol=1e-12)
+    assert np.allclose(Nm, Nm.T, atol=1e-13)
+    mu = np.linalg.eigvalsh(Nm)
+    assert mu.min() > -1e-12 and mu.max() < 1 + 1e-12
+    dh, dn = P.diagonal(k)
+    assert np.allclose(dh.reshape(-1)[sel], np.diag(Hm), atol=1e-13)
+    assert np.allclose(dn.reshape(-1)[sel], np.diag(Nm), atol=1e-13)
+
+
+# ---- energies and sweeps -------------------------------------------------------------------
+
+def _functional_ed(mps, h1, eri, K, N, twoM, twoS, ng):
+    Na, Nb = inputs.electron_counts(N, twoM)
+    H, basis = fock.hamiltonian(K, Na, Nb, h1, eri)
+    psi = S.to_full_vector(mps)
+    beta, c = Q.projector_quadrature(twoS, twoM, ng)
+    pp = sum(cg * fock.apply_site_ops(psi, [Q.site_rotation(b)] * K) for b, cg in zip(beta, c))
+    idx = fock.mask_to_sites(basis, K)
+    return float(psi[idx] @ (H @ pp[idx]) / (psi[idx] @ pp[idx])), float(psi[idx] @ pp[idx])
+
+
+@pytest.mark.parametrize("K,N,twoM,twoS,D,seed", [(4, 4, 0, 0, 8, 1), (5, 5, 1, 3, 8, 2)])
+def test_energy_functional_matches_ed(K, N, twoM, twoS, D, seed):
+    h1, eri = inputs.hubbard_chain(K, 1.0, 4.0)
+    ng = Q.n_exact(K, N, twoM, twoS)
+    labels, tens = inputs.random_mps(K, N, twoM, D, seed)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, ng)
+    E, nP = P.energy(0)
+    E_ed, nP_ed = _functional_ed(P.mps, h1, eri, K, N, twoM, twoS, ng)
+    assert abs(E - E_ed) < 1e-12
+    assert abs(nP - nP_ed) < 1e-13
+    assert 0.0 < nP <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("K,N,twoM,twoS,D", [(4, 4, 0, 0, 16), (4, 4, 2, 2, 16), (4, 4, 0, 2, 16), (6, 6, 0, 0, 64)])
+def test_untruncated_sweeps_reach_exact_spin_state(K, N, twoM, twoS, D):
+    """D at the exact Schmidt rank: sweeps reach the lowest spin-S ED eigenvalue, obtained
+    independently of the projector (S^2 penalty built from creation operators)."""
+    h1, eri = inputs.hubbard_chain(K, 1.0, 4.0)
+    Na, Nb = inputs.electron_counts(N, twoM)
+    e_ed, _, _ = fock.lowest_spin_state(K, Na, Nb, h1, eri, twoS)
+    labels, tens = inputs.random_mps(K, N, twoM, D, 1)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, Q.n_exact(K, N, twoM, twoS))
+    log = S.run_sweeps(P, D, 3, tol_r=1e-9)
+    assert abs(log.sweep_energy[-1] - e_ed) < 1e-10
+    # <S^2> of the projected state, through the same engine with the S^2 MPO of Eq. Sfac
+    P2 = S.Projected(P.mps, M.s2_mpo(K), twoS, twoM, Q.n_exact(K, N, twoM, twoS))
+    P2.build_right(2)
+    s2, _ = P2.energy(0)
+    s = 0.5 * twoS
+    assert abs(s2 - s * (s + 1)) < 1e-10
+
+
+def test_truncated_sweeps_are_variational():
+    K, N, twoM, twoS, D = 6, 6, 0, 0, 12
+    h1, eri = inputs.hubbard_chain(K, 1.0, 4.0)
+    e_ed, _, _ = fock.lowest_spin_state(K, 3, 3, h1, eri, twoS)
+    labels, tens = inputs.random_mps(K, N, twoM, D, 3)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, Q.n_exact(K, N, twoM, twoS))
+    log = S.run_sweeps(P, D, 2)
+    assert all(th >= e_ed - 1e-10 for th in log.theta)
+    E, _ = P.energy(0)
+    E_ed_fn, _ = _functional_ed(P.mps, h1, eri, K, N, twoM, twoS, Q.n_exact(K, N, twoM, twoS))
+    assert abs(E - E_ed_fn) < 1e-10 and E >= e_ed - 1e-10
+
+
+def test_spin_flip_leaves_singlet_functional_unchanged():
+    """alpha <-> beta on every site (with |ab> -> -|ab>) commutes with a spin-free H and with
+    the S=0, M=0 projector, so the functional is unchanged."""
+    K, N, D = 4, 4, 8
+    labels, tens = inputs.random_mps(K, N, 0, D, 9)
+    flip = np.zeros((4, 4)); flip[0, 0] = 1; flip[1, 2] = 1; flip[2, 1] = 1; flip[3, 3] = -1
+    ng = Q.n_exact(K, N, 0, 0)
+    mpo = M.hubbard_mpo(K, 1.0, 4.0)
+    P = S.prepare(labels, tens, mpo, 0, 0, ng)
+    E1, _ = P.energy(0)
+    flipped = [np.einsum("ts,asb->atb", flip, A) for A in P.mps.A]
+    fl_labels = [np.stack([l[:, 0], -l[:, 1]], axis=1) for l in P.mps.labels]
+    # re-sort the bond indices so labels stay sorted by (n, 2m)
+    perms = [np.lexsort((l[:, 1], l[:, 0])) for l in fl_labels]
+    fl_labels = [l[p] for l, p in zip(fl_labels, perms)]
+    flipped = [A[np.ix_(perms[i], range(4), perms[i + 1])] for i, A in enumerate(flipped)]
+    P2 = S.prepare(fl_labels, flipped, mpo, 0, 0, ng)
+    E2, _ = P2.energy(0)
+    assert abs(E1 - E2) < 1e-12
+
+
+# ---- decimation and Davidson ---------------------------------------------------------------
+
+def test_untruncated_decimation_reconstructs_and_is_canonical():
+    K, N, D = 5, 5, 64
+    labels, tens = inputs.random_mps(K, N, 1, 6, 4)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), 1, 1, 2)
+    k = 1
+    ql, qr = P.mps.labels[k], P.mps.labels[k + 2]
+    rng = np.random.default_rng(0)
+    x = np.where(S.two_site_mask(ql, qr), rng.standard_normal((ql.shape[0], 4, 4, qr.shape[0])), 0.0)
+    for move_right in (True, False):
+        Al, Ar, lm, disc = S.decimate(x, ql, qr, D, move_right)
+        rec = np.einsum("asc,cjb->asjb", Al, Ar)
+        assert np.allclose(rec, x / np.linalg.norm(x), atol=1e-13)
+        assert disc < 1e-24
+        if move_right:
+            Lm = Al.reshape(-1, Al.shape[2])
+            assert np.allclose(Lm.T @ Lm, np.eye(Lm.shape[1]), atol=1e-13)
+        else:
+            Rm = Ar.reshape(Ar.shape[0], -1)
+            assert np.allclose(Rm @ Rm.T, np.eye(Rm.shape[0]), atol=1e-13)
+        assert np.all(np.diff(lm[:, 0] * 1000 + lm[:, 1]) >= 0)
+
+
+def test_ordered_truncation_tie_rule():
+    vals = [0.5, 0.3, 0.3 + 1e-13, 0.3, 0.1, 1e-15]
+    tags = [(2, 0, 0), (3, 1, 0), (3, -1, 0), (2, 0, 1), (1, 1, 0), (0, 0, 0)]
+    keep = S.ordered_truncation(vals, tags, 3)
+    # 0.5 first; then the tie cluster {0.3 x 3} ordered by (n, 2m, index): (2,0,1), (3,-1,0), (3,1,0)
+    assert keep == [0, 3, 2]
+    assert S.ordered_truncation(vals, tags, 10) == [0, 3, 2, 1, 4]  # 1e-15 dropped
+
+
+@pytest.mark.parametrize("precond", ["diag", "metric"])
+def test_davidson_matches_library_generalised_eigensolver(precond):
+    """Special case that a library routine solves: random symmetric H, positive-definite N."""
+    n = 60
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((n, n)); H = A + A.T + np.diag(np.arange(n, dtype=float))
+    B = rng.standard_normal((n, n)); Nm = B @ B.T / n + np.eye(n)
+    shape = (n,)
+    ex = sla.eigh(H, Nm, eigvals_only=True)[0]
+    res = S.davidson(lambda v: (H @ v, Nm @ v), rng.standard_normal(n), np.diag(H), np.diag(Nm),
+                     np.ones(shape, bool), tol_r=1e-9, precond=precond, apply_n=lambda v: Nm @ v)
+    assert res.converged
+    assert abs(res.theta - ex) < 1e-10
+    assert abs(res.x @ Nm @ res.x - 1.0) < 1e-10
