@@ -1,0 +1,170 @@
+/*
+ * spmps.h -- C ABI of the GB300 (sm_103a) library for spin-projected matrix product states.
+ *
+ * The library optimises an MPS |Psi> with good particle number N and spin projection M
+ * (Abelian (N, M) block sparsity) for the spin-projected energy functional
+ *     E = <Psi| H P |Psi> / <Psi| P |Psi>,     P = sum_g c_g exp(-i beta_g S_y)
+ * (Li & Chan, arXiv 1703.04789, Eq. efunctional and Eq. pmpo; c_g = (2S+1)/2 w_g d^S_MM(beta_g)
+ * with Gauss-Legendre weights w_g in x = cos(beta)).  Every contraction runs in the library's
+ * CUDA kernels; there is no CPU fallback: without a usable sm_103a device every entry point
+ * that needs one returns SPMPS_ERR_CUDA.
+ *
+ * Conventions shared by all entry points
+ *   - Sites are spatial orbitals k = 0 .. K-1 (Sec. 2.1, last paragraph).  The local basis of a
+ *     site is {|0>, |b>, |a>, |ab>}, index 2*n_alpha + n_beta, |ab> = a+_alpha a+_beta |0>, with
+ *     Jordan-Wigner order alpha before beta on each site (Eq. JWtrans merged per site).
+ *   - Bond i (0..K) carries the quantum numbers (n, 2m) accumulated over sites 0..i-1.  Its
+ *     indices are sorted by (n, 2m); the indices of one label are contiguous.
+ *   - Two-site tensors x, y, z at sites (k, k+1) use the "row-block layout": for each label
+ *     lambda_a of bond k in bond order, one dense row-major block of dim(lambda_a) rows and
+ *     W(lambda_a) columns; the columns run over s = 4*s1 + s2 ascending and, inside s, over the
+ *     indices of the label lambda_a + q(s1) + q(s2) of bond k+2 (absent labels contribute no
+ *     columns).  spmps_x_layout() returns the block table.  Entries outside the (N, M)
+ *     pattern do not exist in this layout.
+ *   - Handles own all device memory they use.  Host arrays passed in are copied; the caller
+ *     keeps ownership.  No C++ exception crosses this interface.
+ *   - Thread safety: one handle must not be used from two threads at once.
+ */
+#ifndef SPMPS_H
+#define SPMPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmps_t* spmps_handle;
+
+typedef enum {
+    SPMPS_OK = 0,
+    SPMPS_ERR_BAD_INPUT = 1,        /* invalid argument; no device work was done          */
+    SPMPS_ERR_NOT_CONVERGED = 2,    /* an iteration hit its cap; best result kept          */
+    SPMPS_ERR_SINGULAR_METRIC = 3,  /* the projected norm matrix has no usable range       */
+    SPMPS_ERR_OOM = 4,              /* device allocation failed                            */
+    SPMPS_ERR_TIMEOUT = 5,          /* a bounded device wait gave up                       */
+    SPMPS_ERR_CUDA = 6,             /* CUDA runtime error (message in spmps_last_error)    */
+    SPMPS_ERR_NAN = 7,              /* NaN or Inf detected in a result                     */
+    SPMPS_ERR_STATE = 8,            /* call out of order (e.g. no Hamiltonian or MPS set)  */
+    SPMPS_ERR_UNSUPPORTED = 9       /* valid request this build does not implement         */
+} spmps_status;
+
+typedef struct {
+    int batched;        /* 1: one grouped launch per contraction phase over all beta points and
+                           blocks (default); 0: one launch per beta point and phase          */
+    int precond;        /* Davidson preconditioner: 0 = diagonal (default), 1 = metric CG    */
+    int cg_steps;       /* CG steps on N_eff t = r for precond == 1 (default 5)               */
+    double dav_tol_r;   /* Davidson residual norm tolerance (default 1e-6)                    */
+    double dav_tol_theta; /* Davidson eigenvalue change tolerance (default 1e-10)             */
+    int dav_max_sub;    /* Davidson subspace size before restart (default 20, max 32)         */
+    int dav_max_iter;   /* Davidson iteration cap per two-site step (default 200)             */
+    int device;         /* CUDA device ordinal (default 0)                                    */
+} spmps_options;
+
+/* Fill *opt with the defaults listed above. */
+void spmps_default_options(spmps_options* opt);
+
+/* Create a handle for K spatial orbitals, N electrons, spin projection M = twoM/2, target spin
+ * S = twoS/2, n_beta Gauss-Legendre points (Eq. pmpo) and maximal bond dimension D.
+ * Checks (SPMPS_ERR_BAD_INPUT): K >= 2, D >= 1, n_beta >= 1, 0 <= N <= 2K, N + twoM even,
+ * twoS >= |twoM|, twoS + N even, both electron counts in [0, K].  n_beta below the exactness
+ * bound of Eq. exactQuadrature is accepted (the projector is then approximate).
+ * opt may be NULL (defaults).  On success *out receives the handle. */
+spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D,
+                          const spmps_options* opt, spmps_handle* out);
+
+spmps_status spmps_destroy(spmps_handle h);
+
+/* Last error message of the handle (static storage when h is NULL); never NULL. */
+const char* spmps_last_error(spmps_handle h);
+
+/* Hamiltonian of an open Hubbard chain over the K sites (Sec. 4.1 with a 1D lattice):
+ * H = -t sum_{k,s} (a+_{k s} a_{k+1 s} + h.c.) + U sum_k n_{k alpha} n_{k beta}. */
+spmps_status spmps_set_hubbard(spmps_handle h, double t, double U);
+
+/* General Hamiltonian of Eq. sqH from one-electron integrals h1 (K*K, row-major) and
+ * chemist two-electron integrals h2 = (pq|rs) (K^4 row-major, may be NULL) plus e_core.
+ * The MPO builder for general h2 is not part of this build: with h2 != NULL the call
+ * returns SPMPS_ERR_UNSUPPORTED unless h2 is zero except (pp|pp) (an on-site U), and h1 must
+ * couple nearest neighbours only (|p-q| <= 1). */
+spmps_status spmps_set_hamiltonian(spmps_handle h, const double* h1, const double* h2, double ecore);
+
+/* Load an MPS.  bond_dims[i] (i = 0..K) is the dimension of bond i (bond_dims[0] =
+ * bond_dims[K] = 1); labels holds 2*sum(bond_dims) ints: (n, 2m) per bond index, bond by bond,
+ * sorted as described above; sites[k] points to a dense row-major D_k x 4 x D_{k+1} array
+ * (entries outside the (N, M) pattern are ignored).  The orthogonality centre is declared
+ * by `center`: sites left of it must be left-canonical and sites right of it right-canonical
+ * for energies to be meaningful (the contractions themselves do not need it). */
+spmps_status spmps_set_mps(spmps_handle h, const int* bond_dims, const int* labels,
+                           const double* const* sites, int center);
+
+/* Number of entries of the two-site tensor at sites (site, site+1) and its block table:
+ * for block j (j < *n_blocks) blocks[5j .. 5j+4] = (index of the left label in bond `site`,
+ * s = 4*s1 + s2, offset of the block's first column inside its row block, rows, columns);
+ * row_block_offsets[i] / row_block_widths[i] give, per left label i, the offset of its row
+ * block and its width W.  Any output pointer may be NULL; array sizes are at most
+ * 16 * (labels of bond `site`) for blocks and (labels of bond `site`) for the two others. */
+spmps_status spmps_x_layout(spmps_handle h, int site, int64_t* n_x, int* n_blocks, int* blocks,
+                            int64_t* row_block_offsets, int* row_block_widths, int* n_left_labels);
+
+/* The projected actions of Eq. geproblem at sites (site, site+1):
+ *   y = sum_g c_g Pi_(N,M) [ H exp(-i beta_g S_y) ]_eff x,   z = sum_g c_g Pi_(N,M) [ exp(-i beta_g S_y) ]_eff x
+ * (Fig. spmpsOpt (b), (c)) with the environments of the current MPS, built on demand.
+ * x, y, z are DEVICE pointers in the row-block layout (n_x doubles each, x read-only; y or z
+ * may be NULL to skip that output).  stream is a cudaStream_t (NULL: the handle's stream);
+ * the call is asynchronous with respect to the host except when environments must be built. */
+spmps_status spmps_apply_heff(spmps_handle h, int site, const double* x, double* y, double* z,
+                              void* stream);
+
+/* Same action, with CUDA events recorded on `stream` between the phases; phase_ms[0..3]
+ * receive the durations of the zero fill, the environment GEMMs over x (phase A), the MPO-leg
+ * combination (phase B) and the output GEMMs (phase C); the call synchronises the stream. */
+spmps_status spmps_apply_heff_timed(spmps_handle h, int site, const double* x, double* y, double* z,
+                                    void* stream, double* phase_ms);
+
+/* Algorithmic flops of one call of spmps_apply_heff at `site`, split as [A, B, C] (symmetry-
+ * allowed block products only: 2*m*n*k per block GEMM, 2*rows*cols per MPO-leg term). */
+spmps_status spmps_apply_flops(spmps_handle h, int site, double* flops3);
+
+/* FP64 fused multiply-add throughput of `device` in TFLOP/s, measured by a kernel of
+ * independent FMA chains on every SM (the roofline denominator of the FP64 path). */
+spmps_status spmps_device_fp64_peak(int device, double* tflops);
+
+/* Same action with HOST buffers: copies x to the device, applies, copies y and z back
+ * (synchronous). */
+spmps_status spmps_apply_heff_host(spmps_handle h, int site, const double* x, double* y, double* z);
+
+/* The current two-site tensor A[site] A[site+1] into a DEVICE buffer of n_x doubles. */
+spmps_status spmps_two_site(spmps_handle h, int site, double* x);
+
+/* Canonicalise the loaded MPS on the device: right-canonical sites 1..K-1, centre on site 0,
+ * norm 1.  Labels whose rank is zero are removed (bond dimensions may shrink). */
+spmps_status spmps_canonicalize(spmps_handle h);
+
+/* n_sweeps two-site sweeps (left-to-right steps k = 0..K-3, then right-to-left k = K-2..0;
+ * centre must be on site 0).  Per step: generalised Davidson for H_eff x = theta N_eff x,
+ * SVD decimation to D (Sec. 2.3.1), environment update.  energies[s] (may be NULL) receives the
+ * energy after sweep s.  Returns SPMPS_ERR_NOT_CONVERGED if any Davidson hit its cap (the
+ * sweep still completes). */
+spmps_status spmps_sweep(spmps_handle h, int n_sweeps, double* energies);
+
+/* Energy functional (Eq. efunctional) and <Psi|P|Psi> at the current centre. */
+spmps_status spmps_energy(spmps_handle h, double* E, double* norm_P);
+
+/* <S^2> of the projected state, through the same engine with the S^2 MPO of Eq. Sfac. */
+spmps_status spmps_expect_s2(spmps_handle h, double* s2);
+
+/* Statistics of the last sweep or apply: counts[0] = Davidson iterations of the last sweep,
+ * counts[1] = projected applies issued, counts[2] = kernel launches issued by the library
+ * since the handle was created; values[0] = algorithmic flops of one projected apply at the
+ * last site applied (symmetry-allowed block products only), values[1] = discarded weight of
+ * the last sweep.  Either pointer may be NULL. */
+spmps_status spmps_stats(spmps_handle h, int64_t* counts, double* values);
+
+/* Quadrature used by the handle: beta_g and c_g (n_beta each, host arrays). */
+spmps_status spmps_quadrature(spmps_handle h, double* beta, double* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMPS_H */

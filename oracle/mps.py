@@ -178,6 +178,28 @@ class Projected:
             out.append(np.where(mask, acc, 0.0))
         return tuple(out)
 
+    def apply_rows(self, x, k, rows, which=("h", "n")):
+        """The same projected action restricted to the bra rows ``rows`` of the left bond
+        (a subset of output entries, for checks at sizes where the full output is too slow)."""
+        ql, qr = self.mps.labels[k], self.mps.labels[k + 2]
+        mask = two_site_mask(ql, qr)[rows]
+        out = []
+        for kind in which:
+            acc = np.zeros((len(rows),) + x.shape[1:])
+            for g, cg in enumerate(self.c):
+                if kind == "h":
+                    L, R = self.Lh[g][k][rows], self.Rh[g][k + 2]
+                    W1, W2 = self.Wh[g][k], self.Wh[g][k + 1]
+                else:
+                    L, R = self.Ln[g][k][rows], self.Rn[g][k + 2]
+                    W1, W2 = self.Wn[g][k], self.Wn[g][k + 1]
+                T = np.einsum("awc,ctid->awtid", L, x)
+                T = np.einsum("awtid,wvst->avsid", T, W1)
+                T = np.einsum("avsid,vuji->asjud", T, W2)
+                acc += cg * np.einsum("asjud,bud->asjb", T, R)
+            out.append(np.where(mask, acc, 0.0))
+        return tuple(out)
+
     def diagonal(self, k):
         """Diagonals of H_eff and N_eff at sites (k, k+1) (preconditioner input)."""
         ql, qr = self.mps.labels[k], self.mps.labels[k + 2]

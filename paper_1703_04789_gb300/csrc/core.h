@@ -1,0 +1,163 @@
+// Internal structures of the SP-MPS library: bond labels, block layouts, MPOs, contraction
+// plans and the device-side task records consumed by the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace spmps {
+
+// Local basis {|0>, |b>, |a>, |ab>} (index 2*n_alpha + n_beta): particle number and 2*Sz.
+constexpr int kLocalN[4] = {0, 1, 1, 2};
+constexpr int kLocal2M[4] = {0, -1, 1, 0};
+
+inline int qn_n(int ns, int s) { return ns == 4 ? kLocalN[s] : kLocalN[s >> 2] + kLocalN[s & 3]; }
+inline int qn_m(int ns, int s) { return ns == 4 ? kLocal2M[s] : kLocal2M[s >> 2] + kLocal2M[s & 3]; }
+
+// ---------------------------------------------------------------------------------------------
+// Bonds: labels (n, 2m) sorted, contiguous; N-groups = runs of labels with equal n.
+struct Label {
+    int n, tm, dim;
+    int off;    // first index of the label on the bond
+    int group;  // index of its N-group
+};
+struct Group {
+    int n, off, dim;   // first index and total dimension of the run
+    int first, count;  // labels [first, first+count)
+};
+struct Bond {
+    std::vector<Label> labels;
+    std::vector<Group> groups;
+    int D = 0;
+    int find(int n, int tm) const;
+    int group_of(int n) const;
+    void finalize();  // fills off, group, groups, D from (n, tm, dim)
+};
+
+// Row-block layout of a tensor with rows on the labels of a left bond and columns over
+// (local index s in [0, ns), indices of the right label lambda + q(s)).
+struct RowBlockLayout {
+    int ns = 0;
+    std::vector<int64_t> row_off;  // per left label
+    std::vector<int> width;        // per left label
+    std::vector<int> seg_col;      // [l*ns + s]: column offset of segment s, -1 if absent
+    std::vector<int> seg_label;    // [l*ns + s]: right label index, -1 if absent
+    int64_t size = 0;
+};
+RowBlockLayout make_row_block_layout(const Bond& left, const Bond& right, int ns);
+
+// Column layout of the M-dense intermediates: for base particle number n0 and local index s,
+// the columns of the right N-group with n = n0 + sign * n(s).
+struct ColLayout {
+    std::vector<int> col;    // [s] column offset, -1 if the group is absent
+    std::vector<int> group;  // [s] group index on the right bond, -1 if absent
+    int width = 0;
+};
+ColLayout make_col_layout(const Bond& right, int n0, int ns, int sign);
+
+// ---------------------------------------------------------------------------------------------
+// MPO: W[k][((wl*dwr + wr)*4 + s)*4 + t], s = output (bra) index, t = input (ket) index.
+struct MPO {
+    int K = 0;
+    std::vector<int> dw;                 // K+1 bond dimensions, dw[0] = dw[K] = 1
+    std::vector<std::vector<int>> cn;    // per bond, per channel: particle-number charge
+    std::vector<std::vector<double>> W;  // per site
+    double& at(int k, int wl, int wr, int s, int t) {
+        return W[k][((static_cast<size_t>(wl) * dw[k + 1] + wr) * 4 + s) * 4 + t];
+    }
+    double get(int k, int wl, int wr, int s, int t) const {
+        return W[k][((static_cast<size_t>(wl) * dw[k + 1] + wr) * 4 + s) * 4 + t];
+    }
+    bool finalize_charges(std::string* err);  // derive cn from the nonzero pattern
+};
+MPO mpo_hubbard(int K, double t, double U);
+// General nearest-neighbour one-band Hamiltonian: on-site energies eps (K), hoppings hop (K-1)
+// between sites k and k+1, on-site repulsions U (K) and a constant.
+MPO mpo_nearest_neighbour(int K, const std::vector<double>& eps, const std::vector<double>& hop,
+                          const std::vector<double>& U, double ecore);
+MPO mpo_s2(int K);
+MPO mpo_identity(int K);
+MPO mpo_rotated(const MPO& m, double beta);  // W . r(beta) on the ket leg (Eq. expSy)
+
+// Quadrature (Eq. pmpo): Gauss-Legendre nodes/weights on [-1, 1] and Wigner small d.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+double wigner_small_d(int two_j, int two_mp, int two_m, double beta);
+void site_rotation(double beta, double r[16]);
+
+// ---------------------------------------------------------------------------------------------
+// Device task records.  Pointers are "slot handles": slot in the top 8 bits, element offset in
+// the low 56 bits; the kernels resolve them against a table of base pointers.
+constexpr int kMaxSlots = 16;
+inline uint64_t handle(int slot, int64_t off) {
+    return (static_cast<uint64_t>(slot) << 56) | static_cast<uint64_t>(off);
+}
+struct Slots {
+    double* p[kMaxSlots];
+};
+
+// C (M x N) = sum over segments of alpha * A(M x K) B(K x N); C(i, j) is stored at
+// C[i*ldc + cmap[j]] (cmap = -1: j).  A(i, k) = A[i*a_rs + k*a_cs], B(k, j) = B[k*b_rs + j*b_cs].
+struct GemmTask {
+    uint64_t c;
+    int cmap;  // offset into the plan's column-map array, -1 for identity
+    int M, N, ldc;
+    int seg0, nseg;
+    int pad;
+};
+struct GemmSeg {
+    uint64_t a, b;
+    int K, a_rs, a_cs, b_rs, b_cs;
+    double alpha;
+};
+struct GemmTile {
+    int task, m0, n0, shape;  // shape: 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32
+};
+
+// dst (rows x cols, ld) = sum over terms of coef * src (rows x cols, ld_src).
+struct CombOut {
+    uint64_t dst;
+    int rows, cols, ld;
+    int term0, nterm;
+    int pad;
+};
+struct CombTerm {
+    uint64_t src;
+    int ld;
+    int pad;
+    double coef;
+};
+
+// Diagonal of the projected operators: for output block b, element (i, j) of the block
+// (rows x cols at x offset off, row stride ld) gets sum over terms of
+// coef * Ld[i*(gl+1) + i0] * Rd[j*(gr+1) + j0] with the term's own L/R diagonal starts.
+struct DiagBlock {
+    int64_t off;
+    int rows, cols, ld;
+    int term0, nterm;
+    int out;  // 0 = H (y), 1 = N (z)
+};
+struct DiagTerm {
+    uint64_t l, r;  // handle of the first diagonal element used
+    int l_step, r_step;
+    double coef;
+};
+
+// A host-side plan of grouped GEMMs.
+struct GemmPlan {
+    std::vector<GemmTask> tasks;
+    std::vector<GemmSeg> segs;
+    std::vector<GemmTile> tiles;
+    std::vector<int> cmaps;
+    double flops = 0.0;
+    void add_tiles();  // tiles of the shape with the least padding per task
+    void clear() { tasks.clear(); segs.clear(); tiles.clear(); cmaps.clear(); flops = 0.0; }
+};
+struct CombPlan {
+    std::vector<CombOut> outs;
+    std::vector<CombTerm> terms;
+    double flops = 0.0;
+    void clear() { outs.clear(); terms.clear(); flops = 0.0; }
+};
+
+}  // namespace spmps

@@ -1,0 +1,147 @@
+// The SP-MPS handle: device state, environment cache and the contraction planner.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/spmps.h"
+#include "core.h"
+#include "kernels.h"
+
+namespace spmps {
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevMem& operator=(DevMem&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevMem() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t nb) {
+        if (nb <= bytes && p) return cudaSuccess;
+        release();
+        size_t want = nb < 256 ? 256 : nb;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        bytes = want;
+        return cudaSuccess;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Per-op layout of one environment tensor on one bond: block (w, G) of gdim(G) x gdim(G')
+// with G' the group of n(G) - cn[w]; -1 where absent.
+struct EnvLayout {
+    int n_groups = 0;
+    std::vector<int64_t> off;  // [w * n_groups + G]
+    std::vector<int> ld;       // [w * n_groups + G] = gdim(G')
+    int64_t size = 0;
+};
+EnvLayout make_env_layout(const Bond& b, const std::vector<int>& cn);
+
+// A set of operators sharing the environment machinery: H and the projector norm (identity)
+// for the energy; S^2 for its expectation value.
+struct OpSet {
+    std::vector<MPO> mpo;                  // per op, unrotated
+    std::vector<std::vector<MPO>> rot;     // [op][g], rotation on the ket leg
+    int n_ops() const { return static_cast<int>(mpo.size()); }
+};
+
+struct EnvStore {
+    DevMem buf;
+    std::vector<EnvLayout> lay;    // per op
+    std::vector<int64_t> base;     // [op * G + g]
+    int64_t total = 0;
+    bool valid = false;
+};
+
+// A three-phase contraction plan (GEMM, MPO-leg combination, GEMM), uploaded to the device.
+struct Plan {
+    GemmPlan A, C;
+    CombPlan B;
+    std::vector<int> tileA_rng, tileC_rng, combB_rng;  // [op * G + g] .. [op * G + g + 1]
+    int64_t t1_size = 0, t2_size = 0;
+    double flops = 0.0;
+    double flops_op[4] = {0, 0, 0, 0};
+    DevMem d_tasksA, d_segsA, d_tilesA, d_cmapsA, d_outsB, d_termsB, d_tasksC, d_segsC, d_tilesC, d_cmapsC;
+    // diagonal (apply plans only)
+    std::vector<DiagBlock> diag_blocks;
+    std::vector<DiagTerm> diag_terms;
+    DevMem d_diag_blocks, d_diag_terms;
+    bool ready = false;
+};
+
+}  // namespace spmps
+
+struct spmps_t {
+    int K = 0, N = 0, twoM = 0, twoS = 0, G = 0, D = 0;
+    spmps_options opt{};
+    std::string err;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<double> beta, cg;
+
+    bool has_ham = false, has_mps = false;
+    spmps::OpSet ops;        // H, N
+    std::vector<spmps::Bond> bonds;           // K+1
+    std::vector<spmps::RowBlockLayout> alay;  // per site, ns = 4
+    std::vector<std::unique_ptr<spmps::DevMem>> A;  // per site
+    int center = 0;
+    std::vector<spmps::EnvStore> Lenv, Renv;  // per bond
+    std::vector<std::unique_ptr<spmps::Plan>> apply_plans;  // per site
+    spmps::DevMem work1, work2, partial;
+    spmps::DevMem xbuf, ybuf, zbuf;  // host-API staging
+    int64_t launches = 0, applies = 0, dav_iters = 0;
+    double last_apply_flops = 0.0, last_discarded = 0.0;
+};
+
+namespace spmps {
+namespace eng {
+
+spmps_status fail(spmps_t* h, spmps_status st, const std::string& msg);
+spmps_status cuda_fail(spmps_t* h, cudaError_t e, const char* where);
+
+template <class T>
+cudaError_t upload(DevMem& m, const std::vector<T>& v, cudaStream_t st) {
+    cudaError_t e = m.ensure(std::max<size_t>(1, v.size()) * sizeof(T));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(m.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+bool validate_plan(const Plan& P, const int64_t* sizes, std::string* why);
+bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why);
+spmps_status plan_upload(spmps_t* h, Plan& P);
+spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t st, cudaEvent_t* ev = nullptr);
+spmps_status update_left(spmps_t* h, int i);
+spmps_status update_right(spmps_t* h, int i);
+spmps_status ensure_envs(spmps_t* h, int k);
+void invalidate_all(spmps_t* h);
+spmps_status get_apply_plan(spmps_t* h, int k, Plan** out);
+spmps_status do_apply(spmps_t* h, int k, const double* x, double* y, double* z, cudaStream_t st,
+                      cudaEvent_t* ev = nullptr);
+spmps_status check_ready(spmps_t* h);
+spmps_status set_ops(spmps_t* h, MPO H);
+spmps_status build_opset(spmps_t* h, const MPO& H, OpSet* out);
+
+}  // namespace eng
+}  // namespace spmps
+
+#define CK(expr)                                                                  \
+    do {                                                                          \
+        cudaError_t _e = (expr);                                                  \
+        if (_e != cudaSuccess) return ::spmps::eng::cuda_fail(h, _e, #expr);      \
+    } while (0)

@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point declared in
+include/spmps.h; argument validation happens before any device work (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from tests.gpu_util import gpu_available, library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "spmps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(spmps_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    path = library()
+    lib = C.CDLL(path)
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_bad_inputs_rejected_without_device_work():
+    from paper_1703_04789_gb300 import Spmps, SpmpsError
+    library()
+    bad = [
+        (1, 2, 0, 0, 4, 8),      # K < 2
+        (4, 3, 0, 1, 4, 8),      # N + 2M odd
+        (4, 4, 2, 0, 4, 8),      # 2S < |2M|
+        (4, 4, 0, 1, 4, 8),      # 2S + N odd
+        (4, 9, 1, 1, 4, 8),      # N > 2K
+        (4, 4, 0, 0, 0, 8),      # n_beta < 1
+        (4, 4, 0, 0, 4, 0),      # D < 1
+        (4, 6, 6, 6, 4, 8),      # N_alpha = 6 > K
+    ]
+    for args in bad:
+        with pytest.raises(SpmpsError) as ei:
+            Spmps(*args)
+        assert ei.value.status == 1, args
+
+
+def test_no_silent_fallback_without_gpu():
+    if gpu_available():
+        pytest.skip("a GPU is present")
+    from paper_1703_04789_gb300 import Spmps, SpmpsError
+    library()
+    with pytest.raises(SpmpsError) as ei:
+        Spmps(4, 4, 0, 0, 2, 8)
+    assert ei.value.status == 6  # SPMPS_ERR_CUDA
