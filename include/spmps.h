@@ -148,6 +148,14 @@ spmps_status spmps_canonicalize(spmps_handle h);
  * sweep still completes). */
 spmps_status spmps_sweep(spmps_handle h, int n_sweeps, double* energies);
 
+/* One two-site step at sites (site, site+1) with the centre inside the pair: generalised
+ * Davidson from the current two-site tensor, decimation to D, environment update.
+ * move_right != 0 leaves site `site` left-canonical and the centre on site+1; otherwise site+1
+ * becomes right-canonical and the centre moves to `site`.  theta (may be NULL) receives the
+ * lowest generalised eigenvalue, iterations (may be NULL) the Davidson iteration count.
+ * Returns SPMPS_ERR_NOT_CONVERGED (after finishing the step) when Davidson hit its cap. */
+spmps_status spmps_optimize_step(spmps_handle h, int site, int move_right, double* theta, int* iterations);
+
 /* Energy functional (Eq. efunctional) and <Psi|P|Psi> at the current centre. */
 spmps_status spmps_energy(spmps_handle h, double* E, double* norm_P);
 

@@ -74,6 +74,7 @@ def load_library(path: str | None = None):
         "spmps_two_site": (i, [H, i, C.c_void_p]),
         "spmps_canonicalize": (i, [H]),
         "spmps_sweep": (i, [H, i, P(d)]),
+        "spmps_optimize_step": (i, [H, i, i, P(d), P(i)]),
         "spmps_energy": (i, [H, P(d), P(d)]),
         "spmps_expect_s2": (i, [H, P(d)]),
         "spmps_stats": (i, [H, P(i64), P(d)]),
@@ -246,6 +247,14 @@ class Spmps:
         if st != 0 and not (allow_not_converged and st == 2):
             self._check(st)
         return e[:n_sweeps], st
+
+    def optimize_step(self, site: int, move_right: bool, allow_not_converged: bool = False):
+        th = C.c_double()
+        it = C.c_int()
+        st = self.lib.spmps_optimize_step(self._h, site, 1 if move_right else 0, C.byref(th), C.byref(it))
+        if st != 0 and not (allow_not_converged and st == 2):
+            self._check(st)
+        return th.value, it.value
 
     def energy(self):
         E = C.c_double()

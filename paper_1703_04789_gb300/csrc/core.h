@@ -111,7 +111,7 @@ struct GemmSeg {
     double alpha;
 };
 struct GemmTile {
-    int task, m0, n0, shape;  // shape: 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32
+    int task, m0, n0, shape;  // shape: 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32, 5 8x4 split-K
 };
 
 // dst (rows x cols, ld) = sum over terms of coef * src (rows x cols, ld_src).

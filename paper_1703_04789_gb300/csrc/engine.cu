@@ -138,7 +138,7 @@ bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why) {
         }
     }
     for (const GemmTile& t : G.tiles)
-        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 4) {
+        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 5) {
             *why = "bad tile";
             return false;
         }

@@ -98,6 +98,14 @@ void GemmPlan::add_tiles() {
     tiles.clear();
     for (size_t t = 0; t < tasks.size(); ++t) {
         const GemmTask& T = tasks[t];
+        int64_t ktot = 0;
+        for (int q = 0; q < T.nseg; ++q) ktot += segs[T.seg0 + q].K;
+        // long reductions over small outputs: split K across the lanes of a warp (shape 5)
+        if (ktot >= 96 && static_cast<int64_t>(T.M) * T.N <= 1024) {
+            for (int m0 = 0; m0 < T.M; m0 += 8)
+                for (int n0 = 0; n0 < T.N; n0 += 4) tiles.push_back(GemmTile{static_cast<int>(t), m0, n0, 5});
+            continue;
+        }
         int best = 0;
         int64_t best_area = -1;
         for (int s = 0; s < 5; ++s) {

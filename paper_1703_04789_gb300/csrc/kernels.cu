@@ -77,6 +77,53 @@ __device__ __forceinline__ void gemm_tile(const Slots& S, const GemmTask& T, con
     }
 }
 
+// Split-K tile (shape 5): 8 x 4 outputs per warp; lane l accumulates the k indices congruent to
+// l mod 32 of every segment, then a recursive-halving shuffle reduce-scatter (31 shuffles)
+// leaves output l (row-major in the 8 x 4 tile) on lane l.
+__device__ __forceinline__ void gemm_tile_splitk(const Slots& S, const GemmTask& T, const GemmSeg* __restrict__ segs,
+                                                 const int* __restrict__ cmaps, int m0, int n0, int lane) {
+    double v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = 0.0;
+    const int mr = min(8, T.M - m0), nc = min(4, T.N - n0);
+    for (int sgi = 0; sgi < T.nseg; ++sgi) {
+        const GemmSeg sg = segs[T.seg0 + sgi];
+        const double* __restrict__ A = resolve(S, sg.a) + static_cast<int64_t>(m0) * sg.a_rs;
+        const double* __restrict__ B = resolve(S, sg.b) + static_cast<int64_t>(n0) * sg.b_cs;
+        const double al = sg.alpha;
+        for (int k = lane; k < sg.K; k += 32) {
+            double a[8], b[4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                a[i] = i < mr ? al * __ldg(A + static_cast<int64_t>(i) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs) : 0.0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                b[j] = j < nc ? __ldg(B + static_cast<int64_t>(k) * sg.b_rs + static_cast<int64_t>(j) * sg.b_cs) : 0.0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[i * 4 + j] = fma(a[i], b[j], v[i * 4 + j]);
+        }
+    }
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int half = 16 >> st, bit = 16 >> st;
+        const bool up = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double send = up ? v[i] : v[i + half];
+            const double keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    const int i = lane >> 2, j = lane & 3;
+    if (i < mr && j < nc) {
+        const int* cm = T.cmap >= 0 ? cmaps + T.cmap : nullptr;
+        const int64_t cc = cm ? cm[n0 + j] : n0 + j;
+        resolve(S, T.c)[static_cast<int64_t>(m0 + i) * T.ldc + cc] = v[0];
+    }
+}
+
 __global__ void __launch_bounds__(128) k_gemm_f64(Slots S, const GemmTask* __restrict__ tasks,
                                                   const GemmSeg* __restrict__ segs, const GemmTile* __restrict__ tiles,
                                                   const int* __restrict__ cmaps, int n_tiles) {
@@ -90,6 +137,7 @@ __global__ void __launch_bounds__(128) k_gemm_f64(Slots S, const GemmTask* __res
         case 2: gemm_tile<8, 4, 8, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 3: gemm_tile<8, 4, 4, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 4: gemm_tile<4, 8, 2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 5: gemm_tile_splitk(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         default: gemm_tile<8, 4, 2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
     }
 }

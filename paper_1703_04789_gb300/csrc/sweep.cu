@@ -608,6 +608,40 @@ spmps_status spmps_canonicalize(spmps_handle h) {
     return SPMPS_OK;
 }
 
+spmps_status spmps_optimize_step(spmps_handle h, int site, int move_right, double* theta, int* iterations) {
+    spmps_status st = check_ready(h);
+    if (st != SPMPS_OK) return st;
+    if (site < 0 || site > h->K - 2) return fail(h, SPMPS_ERR_BAD_INPUT, "site out of range");
+    if (h->center != site && h->center != site + 1) return fail(h, SPMPS_ERR_STATE, "the centre must be in the pair");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, SPMPS_ERR_CUDA, "cudaSetDevice");
+    DavBuffers DB;
+    DecBuffers EB;
+    DevMem x0;
+    const int64_t n = x_size(h, site);
+    CK(x0.ensure(std::max<int64_t>(n, 1) * sizeof(double)));
+    st = spmps_two_site(h, site, x0.as<double>());
+    if (st != SPMPS_OK) return st;
+    DavidsonOut out;
+    st = davidson(h, site, x0.as<double>(), DB, &out);
+    if (st != SPMPS_OK) return st;
+    double disc = 0.0;
+    st = decimate(h, site, DB.x.as<double>(), h->D, move_right != 0, EB, &disc);
+    if (st != SPMPS_OK) return st;
+    h->last_discarded = disc;
+    if (move_right) {
+        st = update_left(h, site);
+        h->center = site + 1;
+    } else {
+        st = update_right(h, site + 1);
+        h->center = site;
+    }
+    if (st != SPMPS_OK) return st;
+    if (theta) *theta = out.theta;
+    if (iterations) *iterations = out.iters;
+    if (!out.converged) return fail(h, SPMPS_ERR_NOT_CONVERGED, "Davidson reached its iteration cap");
+    return SPMPS_OK;
+}
+
 spmps_status spmps_sweep(spmps_handle h, int n_sweeps, double* energies) {
     spmps_status st = check_ready(h);
     if (st != SPMPS_OK) return st;
