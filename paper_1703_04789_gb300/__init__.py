@@ -69,6 +69,7 @@ def load_library(path: str | None = None):
         "spmps_apply_heff": (i, [H, i, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "spmps_apply_heff_host": (i, [H, i, P(d), P(d), P(d)]),
         "spmps_apply_heff_timed": (i, [H, i, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(d)]),
+        "spmps_apply_heff_noalloc": (i, [H, i, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "spmps_apply_flops": (i, [H, i, P(d)]),
         "spmps_device_fp64_peak": (i, [i, P(d)]),
         "spmps_two_site": (i, [H, i, C.c_void_p]),
@@ -214,6 +215,14 @@ class Spmps:
         if stream is not None:
             s = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._check(self.lib.spmps_apply_heff(self._h, site, ptr(x), ptr(y), ptr(z), s))
+
+    def apply_heff_noalloc(self, site: int, x, y=None, z=None, stream=None):
+        """The projected action with no device allocation (intermediates in the library's fixed
+        static scratch); needs a previous apply_heff for the same site."""
+        def ptr(t):
+            return None if t is None else C.c_void_p(t if isinstance(t, int) else t.data_ptr())
+        s = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        self._check(self.lib.spmps_apply_heff_noalloc(self._h, site, ptr(x), ptr(y), ptr(z), s))
 
     def apply_heff_timed(self, site: int, x, y, z, stream=None):
         """Device apply with per-phase CUDA-event times (ms): [zero fill, A, B, C]."""
