@@ -2,15 +2,18 @@
 """Benchmark of the SP-MPS hot path on GB300 (one JSON line on rank 0).
 
 Workload: open Hubbard chain L=24, t=1, U=4, half filling, D=256, n_beta=8 Gauss-Legendre
-points, targets S=0 (2M=0) and S=1 (2M=2); seeded random (N, M)-symmetric MPS with the bond
-structure of that D.  One step = the projected action (y = H_eff x and z = N_eff x over all
-beta points, Eq. geproblem) at the middle two-site position for both targets.
-Metric: algorithmic TFLOP/s of the projected action (symmetry-allowed block products only).
+points, targets S=0 (2M=0) and S=1 (2M=2).  Set-up (untimed): seeded random (N, M)-symmetric MPS,
+canonicalised on the GPU, W warm-up two-site sweeps, checkpoint.  One step = for each target,
+restore the checkpoint (untimed) and run one full two-site sweep (2K-3 steps of generalised
+Davidson with the projected H_eff/N_eff action, decimation to D, environment updates): every row
+of the hot path.  Value = algorithmic TFLOP/s of the projected actions issued in the timed sweeps
+over the sweep time (symmetry-allowed block products only); sweep seconds are reported beside.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (plain float64 NumPy) on the host cores on a bounded
-sample of the same workload.  N > 1 (under torchrun) runs independent replicas.
+sample of the same workload (one projected action per step).  N > 1 (under torchrun) runs
+independent replicas.
 """
 from __future__ import annotations
 
@@ -31,10 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "SP-MPS sweep time & projected H_eff·x TFLOP/s vs FP64 plain at 1e-6 Eh"
 WORKLOAD = {
     "workload": "Hubbard chain L=24 open, t=1, U=4, N=24, targets (2M,2S)=(0,0) and (2,2), D=256, "
-                "n_beta=8; step = projected H_eff/N_eff action at sites (11,12) for both targets",
+                "n_beta=8; step = one two-site sweep per target from a checkpoint taken after the warm-up sweeps",
     "L": 24, "N": 24, "D": 256, "n_beta": 8, "U": 4.0, "targets": [[0, 0], [2, 2]], "site": 11,
-    "mps": "seeded random (N,M)-symmetric MPS, inputs.random_mps(seed=2)",
-    "l2": "flushed between timed steps (256 MiB write)",
+    "mps": "seeded random (N,M)-symmetric MPS, inputs.random_mps(seed=2), canonicalised on the GPU",
+    "davidson": "diagonal preconditioner, |r| < 1e-6 and |dtheta| < 1e-10, subspace 20, cap 200",
+    "l2": "flushed before every timed sweep (256 MiB write); environments of all bonds exceed L2",
 }
 
 
@@ -90,7 +94,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def _setup_handles(torch):
+def _setup_handles(args):
     from paper_1703_04789_gb300 import Spmps, inputs
     W = WORKLOAD
     handles = []
@@ -99,12 +103,11 @@ def _setup_handles(torch):
         dev = Spmps(W["L"], W["N"], twoM, twoS, W["n_beta"], W["D"])
         dev.set_hubbard(1.0, W["U"])
         dev.set_mps(labels, tens, center=0)
-        lay = dev.x_layout(W["site"])
-        rng = np.random.default_rng(11)
-        xh = rng.standard_normal(lay["n_x"])
-        x = torch.tensor(xh, device="cuda")
-        handles.append({"dev": dev, "x": x, "xh": xh, "y": torch.empty_like(x), "z": torch.empty_like(x),
-                        "flops": dev.apply_flops(W["site"]), "n_x": lay["n_x"]})
+        dev.canonicalize()
+        e_warm, _ = dev.sweep(args.warmup)
+        ckpt = dev.get_mps()
+        handles.append({"dev": dev, "ckpt": ckpt, "twoS": twoS, "e_warm": [float(e) for e in e_warm],
+                        "ckpt_bytes": int(sum(t.size for t in ckpt[1]) * 8)})
     return handles
 
 
@@ -117,88 +120,94 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_1703_04789_gb300 import build as B, device_fp64_peak
     B.build()
-    handles = _setup_handles(torch)
-    site = WORKLOAD["site"]
-    stream = torch.cuda.Stream()
+    handles = _setup_handles(args)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    flops_step = sum(float(h["flops"].sum()) for h in handles)
-    gemm_flops_step = sum(float(h["flops"][0] + h["flops"][2]) for h in handles)
-
-    def step(timed_phases=None):
-        for h in handles:
-            ms = h["dev"].apply_heff_timed(site, h["x"], h["y"], h["z"], stream=stream)
-            if timed_phases is not None:
-                timed_phases.append(ms)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    streams = [torch.cuda.ExternalStream(h["dev"].stream_handle()) for h in handles]
     launches0 = sum(h["dev"].stats()["launches"] for h in handles)
+    flops0 = [h["dev"].stats()["apply_flops_total"] for h in handles]
+    for h in handles:
+        h["dev"].profile(True)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms = []
-    phases = []
+    sweep_ms = [[] for _ in handles]
+    energies = [[] for _ in handles]
+    iters = [[] for _ in handles]
     for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(phases)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+        for hi, h in enumerate(handles):
+            dev = h["dev"]
+            dev.set_mps(*h["ckpt"][:2], center=h["ckpt"][2])
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(streams[hi])
+            E, st = dev.sweep(1)
+            e1.record(streams[hi])
+            e1.synchronize()
+            sweep_ms[hi].append(e0.elapsed_time(e1))
+            energies[hi].append(float(E[0]))
+            iters[hi].append(dev.stats()["davidson_iterations"])
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
+    gemm = [h["dev"].kernel_stats(0) for h in handles]
+    comb = [h["dev"].kernel_stats(1) for h in handles]
+    for h in handles:
+        h["dev"].profile(False)
     launches = sum(h["dev"].stats()["launches"] for h in handles) - launches0
-    total_ms = sum(step_ms)
+    apply_flops = sum(h["dev"].stats()["apply_flops_total"] - f0 for h, f0 in zip(handles, flops0))
+    total_ms = sum(sum(m) for m in sweep_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = flops_step * args.steps * world / (total_ms * 1e-3) / 1e12
+    value = apply_flops * world / (total_ms * 1e-3) / 1e12
 
-    # end to end through the host C-ABI entry point (H2D of x, D2H of y and z inside)
+    # end to end through the host C ABI: checkpoint upload (host -> device), sweep, energy read-back
     e2e_ms = []
-    for _ in range(max(1, args.steps)):
-        flush.zero_()
-        torch.cuda.synchronize()
+    for _ in range(max(1, min(args.steps, 2))):
         t0 = time.perf_counter()
         for h in handles:
-            h["dev"].apply_heff_host(site, h["xh"])
+            h["dev"].set_mps(*h["ckpt"][:2], center=h["ckpt"][2])
+            h["dev"].sweep(1)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = flops_step * len(e2e_ms) * world / (sum(e2e_ms) * 1e-3) / 1e12
-    h2d = sum(h["n_x"] * 8 for h in handles)
-    d2h = sum(2 * h["n_x"] * 8 for h in handles)
+    per_step_flops = apply_flops / args.steps
+    e2e_value = per_step_flops * len(e2e_ms) * world / (sum(e2e_ms) * 1e-3) / 1e12
+    h2d = sum(h["ckpt_bytes"] for h in handles)
+    d2h = 8 * len(handles)
 
-    gemm_ms = sum(p[1] + p[3] for p in phases)
-    n_gemm_launches = 2 * len(phases)
-    achieved = gemm_flops_step * args.steps / (gemm_ms * 1e-3) / 1e12
+    g_ms = sum(g["ms"] for g in gemm)
+    g_fl = sum(g["flops"] for g in gemm)
+    g_n = sum(g["launches"] for g in gemm)
+    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
     peak = device_fp64_peak(torch.cuda.current_device())
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
-        "roofline": {"bound": "alu", "kernel": "k_gemm_f64 (phases A and C)", "achieved": round(achieved, 6),
-                     "peak": round(peak, 6), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+        "sweep_s": {f"2S={h['twoS']}": round(statistics.mean(m) / 1e3, 4) for h, m in zip(handles, sweep_ms)},
+        "davidson_iterations_per_sweep": {f"2S={h['twoS']}": it for h, it in zip(handles, iters)},
+        "energies": {f"2S={h['twoS']}": [round(e, 10) for e in E] for h, E in zip(handles, energies)},
+        "roofline": {"bound": "alu", "kernel": "k_gemm_f64 (all block GEMMs of the sweep)",
+                     "achieved": round(achieved, 6), "peak": round(peak, 6), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4) if peak else None,
                      "peak_source": "measured: FP64 FMA-chain kernel on all SMs (nominal 1.25)",
-                     "traffic": None, "launches_per_step": n_gemm_launches // max(1, args.steps),
-                     "avg_launch_ms": round(gemm_ms / max(1, n_gemm_launches), 5)},
-        "phase_ms_per_step": [round(sum(p[i] for p in phases) / args.steps, 5) for i in range(4)],
+                     "traffic": None, "launches": g_n, "avg_launch_ms": round(g_ms / max(1, g_n), 5),
+                     "share_of_sweep": round(g_ms / total_ms, 4) if total_ms else None},
+        "comb_kernel": {"launches": sum(c["launches"] for c in comb), "ms": round(sum(c["ms"] for c in comb), 3)},
         "e2e": {"value": round(e2e_value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(flops_per_apply=float(handles[0]["flops"].sum()))
+        line["cpu_baseline"] = cpu_baseline_sample(flops_per_apply=_alg_flops_cpu())
     print(json.dumps(line), flush=True)
 
 
@@ -340,8 +349,8 @@ def _count_apply_flops(struct, k, mpo, G, twoS, twoM):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

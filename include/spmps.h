@@ -59,6 +59,8 @@ typedef struct {
     int dav_max_sub;    /* Davidson subspace size before restart (default 20, max 32)         */
     int dav_max_iter;   /* Davidson iteration cap per two-site step (default 200)             */
     int device;         /* CUDA device ordinal (default 0)                                    */
+    int jacobi_smem_max; /* decimation blocks up to this size are diagonalised in shared memory,
+                            larger ones in global memory (default and maximum 112; 0 = default) */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -178,12 +180,31 @@ spmps_status spmps_energy(spmps_handle h, double* E, double* norm_P);
 /* <S^2> of the projected state, through the same engine with the S^2 MPO of Eq. Sfac. */
 spmps_status spmps_expect_s2(spmps_handle h, double* s2);
 
-/* Statistics of the last sweep or apply: counts[0] = Davidson iterations of the last sweep,
- * counts[1] = projected applies issued, counts[2] = kernel launches issued by the library
- * since the handle was created; values[0] = algorithmic flops of one projected apply at the
- * last site applied (symmetry-allowed block products only), values[1] = discarded weight of
- * the last sweep.  Either pointer may be NULL. */
+/* Statistics: counts[0] = Davidson iterations of the last sweep, counts[1] = projected applies
+ * issued, counts[2] = kernel launches issued by the library since the handle was created;
+ * values[0] = algorithmic flops of one projected apply at the last site applied (symmetry-
+ * allowed block products only), values[1] = discarded weight of the last sweep, values[2] =
+ * algorithmic flops of every projected apply issued since the handle was created.  Either
+ * pointer may be NULL (counts holds 3, values 3). */
 spmps_status spmps_stats(spmps_handle h, int64_t* counts, double* values);
+
+/* Copy the current MPS to host memory (checkpoint).  First call with sites == NULL: fills
+ * bond_dims[0..K] (and *center).  Second call: labels must hold 2 * sum(bond_dims) ints and sites[k]
+ * D_k * 4 * D_{k+1} doubles (dense row-major, zeros outside the (N, M) pattern) -- the format
+ * spmps_set_mps reads.  Any pointer other than bond_dims may be NULL. */
+spmps_status spmps_get_mps(spmps_handle h, int* bond_dims, int* labels, double* const* sites, int* center);
+
+/* The cudaStream_t the handle's own work (sweeps, environment builds) runs on. */
+spmps_status spmps_stream(spmps_handle h, void** stream);
+
+/* Per-launch CUDA-event timing of the library's block-GEMM and MPO-leg kernels (off by default).
+ * enable != 0 switches it on and clears the counters; enable == 0 switches it off. */
+spmps_status spmps_profile(spmps_handle h, int enable);
+
+/* Counters of the profiler for kernel `kind` (0 = k_gemm_f64, 1 = k_comb_f64): launches, total
+ * device time in ms, and the algorithmic flops those launches performed (same rule as
+ * spmps_apply_flops).  Synchronises the handle's stream. */
+spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops);
 
 /* Quadrature used by the handle: beta_g and c_g (n_beta each, host arrays). */
 spmps_status spmps_quadrature(spmps_handle h, double* beta, double* c);

@@ -358,7 +358,7 @@ def _cg_metric(apply_n, r, steps):
 # ---- decimation ---------------------------------------------------------------------------
 
 TIE_RTOL = 1e-10
-DROP_ABS = 1e-14
+DROP_ABS = 1e-7  # dropped weight per singular value < 1e-14 (|x| = 1)
 
 
 def ordered_truncation(values, labels, D):

@@ -38,6 +38,7 @@ class Options(C.Structure):
         ("batched", C.c_int), ("precond", C.c_int), ("cg_steps", C.c_int),
         ("dav_tol_r", C.c_double), ("dav_tol_theta", C.c_double),
         ("dav_max_sub", C.c_int), ("dav_max_iter", C.c_int), ("device", C.c_int),
+        ("jacobi_smem_max", C.c_int),
     ]
 
 
@@ -80,6 +81,10 @@ def load_library(path: str | None = None):
         "spmps_expect_s2": (i, [H, P(d)]),
         "spmps_stats": (i, [H, P(i64), P(d)]),
         "spmps_quadrature": (i, [H, P(d), P(d)]),
+        "spmps_get_mps": (i, [H, P(i), P(i), C.c_void_p, P(i)]),
+        "spmps_stream": (i, [H, P(C.c_void_p)]),
+        "spmps_profile": (i, [H, i]),
+        "spmps_kernel_stats": (i, [H, i, P(i64), P(d), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -97,7 +102,8 @@ class Spmps:
     """One SP-MPS problem on one GPU (spmps_create ... spmps_destroy)."""
 
     def __init__(self, K, N, twoM, twoS, n_beta, D, *, batched=True, precond="diag", cg_steps=5,
-                 dav_tol_r=1e-6, dav_tol_theta=1e-10, dav_max_sub=20, dav_max_iter=200, device=0):
+                 dav_tol_r=1e-6, dav_tol_theta=1e-10, dav_max_sub=20, dav_max_iter=200, device=0,
+                 jacobi_smem_max=0):
         self.lib = load_library()
         o = Options()
         self.lib.spmps_default_options(C.byref(o))
@@ -105,6 +111,7 @@ class Spmps:
         o.precond = {"diag": 0, "metric": 1}[precond]
         o.cg_steps, o.dav_tol_r, o.dav_tol_theta = cg_steps, dav_tol_r, dav_tol_theta
         o.dav_max_sub, o.dav_max_iter, o.device = dav_max_sub, dav_max_iter, device
+        o.jacobi_smem_max = jacobi_smem_max
         h = C.c_void_p()
         self._h = None
         self._check(self.lib.spmps_create(K, N, twoM, twoS, n_beta, D, C.byref(o), C.byref(h)), None)
@@ -278,10 +285,42 @@ class Spmps:
 
     def stats(self):
         c = (C.c_int64 * 3)()
-        v = (C.c_double * 2)()
+        v = (C.c_double * 3)()
         self._check(self.lib.spmps_stats(self._h, c, v))
         return {"davidson_iterations": c[0], "applies": c[1], "launches": c[2],
-                "apply_flops": v[0], "discarded_weight": v[1]}
+                "apply_flops": v[0], "discarded_weight": v[1], "apply_flops_total": v[2]}
+
+    def get_mps(self):
+        """Checkpoint: (labels, tensors, center) in the format set_mps reads."""
+        dims = np.zeros(self.K + 1, dtype=np.int32)
+        cen = C.c_int()
+        self._check(self.lib.spmps_get_mps(self._h, dims.ctypes.data_as(C.POINTER(C.c_int)), None, None, C.byref(cen)))
+        lab = np.zeros(2 * int(dims.sum()), dtype=np.int32)
+        ts = [np.zeros((int(dims[k]), 4, int(dims[k + 1]))) for k in range(self.K)]
+        arr = (C.POINTER(C.c_double) * self.K)(*[_dptr(t) for t in ts])
+        self._check(self.lib.spmps_get_mps(self._h, dims.ctypes.data_as(C.POINTER(C.c_int)),
+                                           lab.ctypes.data_as(C.POINTER(C.c_int)), C.cast(arr, C.c_void_p),
+                                           C.byref(cen)))
+        labels, off = [], 0
+        for b in range(self.K + 1):
+            labels.append(lab[2 * off: 2 * (off + int(dims[b]))].reshape(-1, 2).astype(np.int64))
+            off += int(dims[b])
+        return labels, ts, cen.value
+
+    def stream_handle(self) -> int:
+        p = C.c_void_p()
+        self._check(self.lib.spmps_stream(self._h, C.byref(p)))
+        return p.value or 0
+
+    def profile(self, enable: bool):
+        self._check(self.lib.spmps_profile(self._h, 1 if enable else 0))
+
+    def kernel_stats(self, kind: int):
+        n = C.c_int64()
+        ms = C.c_double()
+        fl = C.c_double()
+        self._check(self.lib.spmps_kernel_stats(self._h, kind, C.byref(n), C.byref(ms), C.byref(fl)))
+        return {"launches": n.value, "ms": ms.value, "flops": fl.value}
 
     def quadrature(self):
         b = np.zeros(self.n_beta)

@@ -96,7 +96,7 @@ struct Slots {
     double* p[kMaxSlots];
 };
 
-// C (M x N) = sum over segments of alpha * A(M x K) B(K x N); C(i, j) is stored at
+// C (M x N) = sum over segments of A(M x K) B(K x N); C(i, j) is stored at
 // C[i*ldc + cmap[j]] (cmap = -1: j).  A(i, k) = A[i*a_rs + k*a_cs], B(k, j) = B[k*b_rs + j*b_cs].
 struct GemmTask {
     uint64_t c;
@@ -108,10 +108,10 @@ struct GemmTask {
 struct GemmSeg {
     uint64_t a, b;
     int K, a_rs, a_cs, b_rs, b_cs;
-    double alpha;
+    int pad;
 };
 struct GemmTile {
-    int task, m0, n0, shape;  // shape: 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32, 5 8x4 split-K
+    int task, m0, n0, shape;  // 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32; 5..19 split-K tiles
 };
 
 // dst (rows x cols, ld) = sum over terms of coef * src (rows x cols, ld_src).

@@ -138,7 +138,7 @@ bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why) {
         }
     }
     for (const GemmTile& t : G.tiles)
-        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 5) {
+        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 19) {
             *why = "bad tile";
             return false;
         }
@@ -192,6 +192,20 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
         }
     };
     std::vector<int> a_task_rng = P.tileA_rng, c_task_rng = P.tileC_rng;
+    auto task_flops = [](const GemmPlan& gp, const std::vector<int>& rng, std::vector<double>& out) {
+        out.assign(rng.size(), 0.0);
+        for (size_t r = 0; r + 1 < rng.size(); ++r)
+            for (int t = rng[r]; t < rng[r + 1]; ++t) {
+                const GemmTask& T = gp.tasks[t];
+                for (int q = 0; q < T.nseg; ++q) out[r] += 2.0 * T.M * T.N * gp.segs[T.seg0 + q].K;
+            }
+    };
+    task_flops(P.A, a_task_rng, P.flopsA_rng);
+    task_flops(P.C, c_task_rng, P.flopsC_rng);
+    P.flopsB_rng.assign(P.combB_rng.size(), 0.0);
+    for (size_t r = 0; r + 1 < P.combB_rng.size(); ++r)
+        for (int o = P.combB_rng[r]; o < P.combB_rng[r + 1]; ++o)
+            P.flopsB_rng[r] += 2.0 * P.B.outs[o].rows * P.B.outs[o].cols * P.B.outs[o].nterm;
     ranges(P.A, a_task_rng, P.tileA_rng);
     ranges(P.C, c_task_rng, P.tileC_rng);
     CK(h->work1.ensure(std::max<int64_t>(1, P.t1_size) * sizeof(double)));
@@ -209,22 +223,37 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
     CK(cudaMemsetAsync(S.p[3], 0, std::max<int64_t>(1, P.t1_size) * sizeof(double), st));
     if (ev) CK(cudaEventRecord(ev[1], st));
     ++h->launches;
+    // flops of a range of (op, g) entries, for the profiler
+    auto range_flops = [&](const std::vector<double>& f, int a, int b) {
+        double acc = 0.0;
+        for (int r = a; r < b && r < static_cast<int>(f.size()); ++r) acc += f[r];
+        return acc;
+    };
     auto runA = [&](int a, int b) -> cudaError_t {
         const int t0 = P.tileA_rng[a], t1 = P.tileA_rng[b];
         ++h->launches;
-        return launch_gemm_f64(S, P.d_tasksA.as<GemmTask>(), P.d_segsA.as<GemmSeg>(),
-                               P.d_tilesA.as<GemmTile>() + t0, P.d_cmapsA.as<int>(), t1 - t0, st);
+        const int rec = h->profile ? prof_begin(h, st, 0, range_flops(P.flopsA_rng, a, b)) : -1;
+        cudaError_t e = launch_gemm_f64(S, P.d_tasksA.as<GemmTask>(), P.d_segsA.as<GemmSeg>(),
+                                        P.d_tilesA.as<GemmTile>() + t0, P.d_cmapsA.as<int>(), t1 - t0, st);
+        if (rec >= 0) prof_end(h, st, rec);
+        return e;
     };
     auto runB = [&](int a, int b) -> cudaError_t {
         const int o0 = P.combB_rng[a], o1 = P.combB_rng[b];
         ++h->launches;
-        return launch_comb_f64(S, P.d_outsB.as<CombOut>() + o0, P.d_termsB.as<CombTerm>(), o1 - o0, st);
+        const int rec = h->profile ? prof_begin(h, st, 1, range_flops(P.flopsB_rng, a, b)) : -1;
+        cudaError_t e = launch_comb_f64(S, P.d_outsB.as<CombOut>() + o0, P.d_termsB.as<CombTerm>(), o1 - o0, st);
+        if (rec >= 0) prof_end(h, st, rec);
+        return e;
     };
     auto runC = [&](int a, int b) -> cudaError_t {
         const int t0 = P.tileC_rng[a], t1 = P.tileC_rng[b];
         ++h->launches;
-        return launch_gemm_f64(S, P.d_tasksC.as<GemmTask>(), P.d_segsC.as<GemmSeg>(),
-                               P.d_tilesC.as<GemmTile>() + t0, P.d_cmapsC.as<int>(), t1 - t0, st);
+        const int rec = h->profile ? prof_begin(h, st, 0, range_flops(P.flopsC_rng, a, b)) : -1;
+        cudaError_t e = launch_gemm_f64(S, P.d_tasksC.as<GemmTask>(), P.d_segsC.as<GemmSeg>(),
+                                        P.d_tilesC.as<GemmTile>() + t0, P.d_cmapsC.as<int>(), t1 - t0, st);
+        if (rec >= 0) prof_end(h, st, rec);
+        return e;
     };
     if (batched) {
         CK(runA(r0, r1));
@@ -317,8 +346,7 @@ void build_left_plan(spmps_t* h, int i, const EnvStore& Lo, const EnvStore& Ln, 
                         sg.b = handle(0, al.row_off[l]);
                         sg.b_rs = al.width[l];
                         sg.b_cs = 1;
-                        sg.alpha = 1.0;
-                        P.A.segs.push_back(sg);
+                                                P.A.segs.push_back(sg);
                         P.A.tasks.push_back(T);
                         P.A.flops += 2.0 * T.M * T.N * sg.K;
                     }
@@ -396,8 +424,7 @@ void build_left_plan(spmps_t* h, int i, const EnvStore& Lo, const EnvStore& Ln, 
                                 sg.b = handle(4, s2 + static_cast<int64_t>(La.off - bl.groups[ga].off) * C2.width + C2.col[s]);
                                 sg.b_rs = C2.width;
                                 sg.b_cs = 1;
-                                sg.alpha = 1.0;
-                                P.C.segs.push_back(sg);
+                                                                P.C.segs.push_back(sg);
                                 P.C.flops += 2.0 * T.M * T.N * sg.K;
                             }
                         T.nseg = static_cast<int>(P.C.segs.size()) - T.seg0;
@@ -473,8 +500,7 @@ void build_right_plan(spmps_t* h, int i, const EnvStore& Ro, const EnvStore& Rn,
                             sg.b = handle(0, al.row_off[lap] + al.seg_col[lap * 4 + t]);
                             sg.b_rs = 1;
                             sg.b_cs = al.width[lap];
-                            sg.alpha = 1.0;
-                            P.A.segs.push_back(sg);
+                                                        P.A.segs.push_back(sg);
                             P.A.tasks.push_back(T);
                             P.A.flops += 2.0 * T.M * T.N * sg.K;
                         }
@@ -553,8 +579,7 @@ void build_right_plan(spmps_t* h, int i, const EnvStore& Ro, const EnvStore& Rn,
                             sg.b = handle(4, s2 + static_cast<int64_t>(Lb.off - br.groups[gb].off) * C2.width + C2.col[s]);
                             sg.b_rs = C2.width;
                             sg.b_cs = 1;
-                            sg.alpha = 1.0;
-                            P.C.segs.push_back(sg);
+                                                        P.C.segs.push_back(sg);
                             P.C.flops += 2.0 * T.M * T.N * sg.K;
                         }
                         T.nseg = static_cast<int>(P.C.segs.size()) - T.seg0;
@@ -664,8 +689,7 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                         sg.b = handle(0, xl.row_off[l]);
                         sg.b_rs = xl.width[l];
                         sg.b_cs = 1;
-                        sg.alpha = 1.0;
-                        P.A.segs.push_back(sg);
+                                                P.A.segs.push_back(sg);
                         P.A.tasks.push_back(T);
                         P.A.flops += 2.0 * T.M * T.N * sg.K;
                     }
@@ -758,8 +782,7 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                         sg.b = handle(6, Re.base[og] + roff + static_cast<int64_t>(Lb.off - br.groups[gb].off) * K);
                         sg.b_rs = 1;
                         sg.b_cs = K;
-                        sg.alpha = 1.0;
-                        P.C.segs.push_back(sg);
+                                                P.C.segs.push_back(sg);
                         P.C.flops += 2.0 * T.M * T.N * K;
                     }
                 }
@@ -980,6 +1003,46 @@ spmps_status do_apply(spmps_t* h, int k, const double* x, double* y, double* z, 
     if (s != SPMPS_OK) return s;
     ++h->applies;
     h->last_apply_flops = P->flops;
+    h->apply_flops_total += (y ? P->flops_op[0] : 0.0) + (z ? P->flops_op[1] : 0.0);
+    return SPMPS_OK;
+}
+
+// ---- profiler ---------------------------------------------------------------------------------
+
+int prof_begin(spmps_t* h, cudaStream_t st, int kind, double flops) {
+    spmps_t::TimerRec r{};
+    if (!h->timers_free.empty()) {
+        r = h->timers_free.back();
+        h->timers_free.pop_back();
+    } else {
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    }
+    r.kind = kind;
+    r.flops = flops;
+    if (cudaEventRecord(r.a, st) != cudaSuccess) {
+        h->timers_free.push_back(r);
+        return -1;
+    }
+    h->timers_live.push_back(r);
+    return static_cast<int>(h->timers_live.size()) - 1;
+}
+
+void prof_end(spmps_t* h, cudaStream_t st, int rec) {
+    cudaEventRecord(h->timers_live[rec].b, st);
+    if (h->timers_live.size() >= 4096) prof_collect(h);
+}
+
+spmps_status prof_collect(spmps_t* h) {
+    for (auto& r : h->timers_live) {
+        CK(cudaEventSynchronize(r.b));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        h->prof_launches[r.kind] += 1;
+        h->prof_ms[r.kind] += ms;
+        h->prof_flops[r.kind] += r.flops;
+        h->timers_free.push_back(r);
+    }
+    h->timers_live.clear();
     return SPMPS_OK;
 }
 
@@ -1036,6 +1099,7 @@ void spmps_default_options(spmps_options* o) {
     o->dav_max_sub = 20;
     o->dav_max_iter = 200;
     o->device = 0;
+    o->jacobi_smem_max = 0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1055,6 +1119,9 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     spmps_default_options(&o);
     if (opt) o = *opt;
     if (o.dav_max_sub < 4 || o.dav_max_sub > 32) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_sub must be in [4, 32]");
+    if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)
+        return fail(nullptr, SPMPS_ERR_BAD_INPUT, "jacobi_smem_max must be in [0, 112]");
+    if (o.jacobi_smem_max == 0) o.jacobi_smem_max = 112;
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
     if (ce != cudaSuccess || ndev <= o.device)
@@ -1091,6 +1158,8 @@ spmps_status spmps_destroy(spmps_handle h) {
     if (!h) return SPMPS_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& r : h->timers_live) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto& r : h->timers_free) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     h->apply_plans.clear();
     h->Lenv.clear();
     h->Renv.clear();
@@ -1357,8 +1426,7 @@ spmps_status spmps_two_site(spmps_handle h, int site, double* x) {
                 sg.b = handle(1, a1.row_off[lc] + a1.seg_col[lc * 4 + s2]);
                 sg.b_rs = a1.width[lc];
                 sg.b_cs = 1;
-                sg.alpha = 1.0;
-                P.A.segs.push_back(sg);
+                                P.A.segs.push_back(sg);
             }
             T.nseg = static_cast<int>(P.A.segs.size()) - T.seg0;
             P.A.tasks.push_back(T);
@@ -1430,7 +1498,76 @@ spmps_status spmps_stats(spmps_handle h, int64_t* counts, double* values) {
     if (values) {
         values[0] = h->last_apply_flops;
         values[1] = h->last_discarded;
+        values[2] = h->apply_flops_total;
     }
+    return SPMPS_OK;
+}
+
+spmps_status spmps_get_mps(spmps_handle h, int* bond_dims, int* labels, double* const* sites, int* center) {
+    spmps_status st = check_ready(h);
+    if (st != SPMPS_OK) return st;
+    if (!bond_dims) return fail(h, SPMPS_ERR_BAD_INPUT, "bond_dims is NULL");
+    const int K = h->K;
+    for (int b = 0; b <= K; ++b) bond_dims[b] = h->bonds[b].D;
+    if (center) *center = h->center;
+    if (labels) {
+        int* lp = labels;
+        for (int b = 0; b <= K; ++b)
+            for (const Label& l : h->bonds[b].labels)
+                for (int i = 0; i < l.dim; ++i) { *lp++ = l.n; *lp++ = l.tm; }
+    }
+    if (!sites) return SPMPS_OK;
+    for (int k = 0; k < K; ++k) {
+        const Bond& bl = h->bonds[k];
+        const Bond& br = h->bonds[k + 1];
+        const RowBlockLayout& L = h->alay[k];
+        std::vector<double> rb(static_cast<size_t>(std::max<int64_t>(L.size, 1)));
+        CK(cudaMemcpyAsync(rb.data(), h->A[k]->p, L.size * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        double* dst = sites[k];
+        if (!dst) continue;
+        std::fill(dst, dst + static_cast<size_t>(bl.D) * 4 * br.D, 0.0);
+        for (size_t la = 0; la < bl.labels.size(); ++la) {
+            const Label& La = bl.labels[la];
+            for (int s = 0; s < 4; ++s) {
+                const int lb = L.seg_label[la * 4 + s];
+                if (lb < 0) continue;
+                const Label& Lb = br.labels[lb];
+                for (int i = 0; i < La.dim; ++i)
+                    for (int j = 0; j < Lb.dim; ++j)
+                        dst[(static_cast<size_t>(La.off + i) * 4 + s) * br.D + Lb.off + j] =
+                            rb[L.row_off[la] + static_cast<int64_t>(i) * L.width[la] + L.seg_col[la * 4 + s] + j];
+            }
+        }
+    }
+    return SPMPS_OK;
+}
+
+spmps_status spmps_stream(spmps_handle h, void** stream) {
+    if (!h || !stream) return fail(h, SPMPS_ERR_BAD_INPUT, "NULL argument");
+    *stream = h->stream;
+    return SPMPS_OK;
+}
+
+spmps_status spmps_profile(spmps_handle h, int enable) {
+    if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
+    spmps_status st = prof_collect(h);
+    if (st != SPMPS_OK) return st;
+    h->profile = enable != 0;
+    if (enable) {
+        for (int k = 0; k < 2; ++k) { h->prof_launches[k] = 0; h->prof_ms[k] = 0.0; h->prof_flops[k] = 0.0; }
+    }
+    return SPMPS_OK;
+}
+
+spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops) {
+    if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
+    if (kind < 0 || kind > 1) return fail(h, SPMPS_ERR_BAD_INPUT, "kind must be 0 or 1");
+    spmps_status st = prof_collect(h);
+    if (st != SPMPS_OK) return st;
+    if (launches) *launches = h->prof_launches[kind];
+    if (ms) *ms = h->prof_ms[kind];
+    if (flops) *flops = h->prof_flops[kind];
     return SPMPS_OK;
 }
 

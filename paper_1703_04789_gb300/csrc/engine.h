@@ -74,6 +74,7 @@ struct Plan {
     GemmPlan A, C;
     CombPlan B;
     std::vector<int> tileA_rng, tileC_rng, combB_rng;  // [op * G + g] .. [op * G + g + 1]
+    std::vector<double> flopsA_rng, flopsB_rng, flopsC_rng;  // algorithmic flops per range
     int64_t t1_size = 0, t2_size = 0;
     double flops = 0.0;
     double flops_op[4] = {0, 0, 0, 0};
@@ -106,7 +107,17 @@ struct spmps_t {
     spmps::DevMem work1, work2, partial;
     spmps::DevMem xbuf, ybuf, zbuf;  // host-API staging
     int64_t launches = 0, applies = 0, dav_iters = 0;
-    double last_apply_flops = 0.0, last_discarded = 0.0;
+    double last_apply_flops = 0.0, last_discarded = 0.0, apply_flops_total = 0.0;
+    // per-launch event profiler
+    struct TimerRec {
+        cudaEvent_t a, b;
+        int kind;
+        double flops;
+    };
+    bool profile = false;
+    std::vector<TimerRec> timers_live, timers_free;
+    int64_t prof_launches[2] = {0, 0};
+    double prof_ms[2] = {0.0, 0.0}, prof_flops[2] = {0.0, 0.0};
 };
 
 namespace spmps {
@@ -136,6 +147,10 @@ spmps_status do_apply(spmps_t* h, int k, const double* x, double* y, double* z, 
 spmps_status check_ready(spmps_t* h);
 spmps_status set_ops(spmps_t* h, MPO H);
 spmps_status build_opset(spmps_t* h, const MPO& H, OpSet* out);
+// profiler: a started record's events are recorded on stream st around one launch
+int prof_begin(spmps_t* h, cudaStream_t st, int kind, double flops);
+void prof_end(spmps_t* h, cudaStream_t st, int rec);
+spmps_status prof_collect(spmps_t* h);
 
 }  // namespace eng
 }  // namespace spmps

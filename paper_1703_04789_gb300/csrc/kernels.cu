@@ -48,12 +48,11 @@ __device__ __forceinline__ void gemm_tile(const Slots& S, const GemmTask& T, con
         const GemmSeg sg = segs[T.seg0 + sgi];
         const double* __restrict__ A = resolve(S, sg.a);
         const double* __restrict__ B = resolve(S, sg.b);
-        const double al = sg.alpha;
         for (int k = 0; k < sg.K; ++k) {
             double a[RM], b[CN];
 #pragma unroll
             for (int i = 0; i < RM; ++i)
-                a[i] = rv[i] ? al * __ldg(A + static_cast<int64_t>(rows[i]) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs)
+                a[i] = rv[i] ? __ldg(A + static_cast<int64_t>(rows[i]) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs)
                              : 0.0;
 #pragma unroll
             for (int j = 0; j < CN; ++j)
@@ -77,37 +76,40 @@ __device__ __forceinline__ void gemm_tile(const Slots& S, const GemmTask& T, con
     }
 }
 
-// Split-K tile (shape 5): 8 x 4 outputs per warp; lane l accumulates the k indices congruent to
-// l mod 32 of every segment, then a recursive-halving shuffle reduce-scatter (31 shuffles)
-// leaves output l (row-major in the 8 x 4 tile) on lane l.
+// Split-K tiles (shapes 5..18): MR x NC outputs per warp (MR, NC in {1,2,4,8}, MR*NC <= 32,
+// a power of two); lane l accumulates the k indices congruent to l mod 32 of every segment, then
+// a recursive-halving shuffle reduce-scatter over log2(MR*NC) lane bits and a butterfly over the
+// remaining bits leaves output (l >> (5 - log2(MR*NC))) on the lanes whose low bits are zero.
+template <int MR, int NC>
 __device__ __forceinline__ void gemm_tile_splitk(const Slots& S, const GemmTask& T, const GemmSeg* __restrict__ segs,
                                                  const int* __restrict__ cmaps, int m0, int n0, int lane) {
-    double v[32];
+    constexpr int NOUT = MR * NC;
+    constexpr int P = NOUT == 1 ? 0 : NOUT == 2 ? 1 : NOUT == 4 ? 2 : NOUT == 8 ? 3 : NOUT == 16 ? 4 : 5;
+    double v[NOUT];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = 0.0;
-    const int mr = min(8, T.M - m0), nc = min(4, T.N - n0);
+    for (int i = 0; i < NOUT; ++i) v[i] = 0.0;
+    const int mr = min(MR, T.M - m0), nc = min(NC, T.N - n0);
     for (int sgi = 0; sgi < T.nseg; ++sgi) {
         const GemmSeg sg = segs[T.seg0 + sgi];
         const double* __restrict__ A = resolve(S, sg.a) + static_cast<int64_t>(m0) * sg.a_rs;
         const double* __restrict__ B = resolve(S, sg.b) + static_cast<int64_t>(n0) * sg.b_cs;
-        const double al = sg.alpha;
         for (int k = lane; k < sg.K; k += 32) {
-            double a[8], b[4];
+            double a[MR], b[NC];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                a[i] = i < mr ? al * __ldg(A + static_cast<int64_t>(i) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs) : 0.0;
+            for (int i = 0; i < MR; ++i)
+                a[i] = i < mr ? __ldg(A + static_cast<int64_t>(i) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs) : 0.0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < NC; ++j)
                 b[j] = j < nc ? __ldg(B + static_cast<int64_t>(k) * sg.b_rs + static_cast<int64_t>(j) * sg.b_cs) : 0.0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < MR; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[i * 4 + j] = fma(a[i], b[j], v[i * 4 + j]);
+                for (int j = 0; j < NC; ++j) v[i * NC + j] = fma(a[i], b[j], v[i * NC + j]);
         }
     }
 #pragma unroll
-    for (int st = 0; st < 5; ++st) {
-        const int half = 16 >> st, bit = 16 >> st;
+    for (int st = 0; st < P; ++st) {
+        const int half = NOUT >> (st + 1), bit = 16 >> st;
         const bool up = (lane & bit) != 0;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
@@ -116,7 +118,10 @@ __device__ __forceinline__ void gemm_tile_splitk(const Slots& S, const GemmTask&
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
         }
     }
-    const int i = lane >> 2, j = lane & 3;
+#pragma unroll
+    for (int bit = 16 >> P; bit > 0; bit >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], bit);
+    if ((lane & ((1 << (5 - P)) - 1)) != 0) return;
+    const int o = lane >> (5 - P), i = o / NC, j = o - i * NC;
     if (i < mr && j < nc) {
         const int* cm = T.cmap >= 0 ? cmaps + T.cmap : nullptr;
         const int64_t cc = cm ? cm[n0 + j] : n0 + j;
@@ -137,7 +142,21 @@ __global__ void __launch_bounds__(128) k_gemm_f64(Slots S, const GemmTask* __res
         case 2: gemm_tile<8, 4, 8, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 3: gemm_tile<8, 4, 4, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 4: gemm_tile<4, 8, 2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 5: gemm_tile_splitk(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 5: gemm_tile_splitk<8, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 6: gemm_tile_splitk<4, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 7: gemm_tile_splitk<4, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 8: gemm_tile_splitk<8, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 9: gemm_tile_splitk<2, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 10: gemm_tile_splitk<4, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 11: gemm_tile_splitk<2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 12: gemm_tile_splitk<8, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 13: gemm_tile_splitk<1, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 14: gemm_tile_splitk<2, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 15: gemm_tile_splitk<4, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 16: gemm_tile_splitk<1, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 17: gemm_tile_splitk<2, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 18: gemm_tile_splitk<1, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+        case 19: gemm_tile_splitk<1, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         default: gemm_tile<8, 4, 2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
     }
 }
@@ -514,7 +533,8 @@ __global__ void __launch_bounds__(512) k_jacobi_batched(double* __restrict__ mat
                                                         double* __restrict__ evals,
                                                         const int64_t* __restrict__ mat_off,
                                                         const int64_t* __restrict__ val_off,
-                                                        const int* __restrict__ dims, int* __restrict__ status) {
+                                                        const int* __restrict__ dims, int smem_dim,
+                                                        int* __restrict__ status) {
     extern __shared__ double smem[];
     __shared__ double cs_sh[2 * 256 + 4], red_sh[40], dg[512];
     __shared__ int pq_sh[2 * 256 + 4];
@@ -523,7 +543,7 @@ __global__ void __launch_bounds__(512) k_jacobi_batched(double* __restrict__ mat
     if (n <= 0) return;
     double* M = mats + mat_off[b];
     double *A, *V;
-    if (n <= kJacobiSmemMax) {
+    if (n <= smem_dim) {  // the launch sized the dynamic shared memory for smem_dim
         A = smem;
         V = smem + n * n;
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = M[e];
@@ -758,16 +778,18 @@ cudaError_t launch_restart_coef(const double* c_new, const double* c_old, int m,
 }
 
 cudaError_t launch_jacobi_batched(double* mats, double* vscratch, double* evals, const int64_t* mat_off,
-                                  const int64_t* val_off, const int* dims, int n_mats, int max_dim, int* status,
-                                  cudaStream_t st) {
+                                  const int64_t* val_off, const int* dims, int n_mats, int max_dim, int smem_limit,
+                                  int* status, cudaStream_t st) {
     if (n_mats <= 0) return cudaSuccess;
     if (max_dim > 512) return cudaErrorInvalidValue;  // pair tables hold at most 256 pairs
-    const int sm_dim = max_dim <= kJacobiSmemMax ? max_dim : 0;
+    // matrices up to sm_dim run in shared memory (A and V), larger ones in global memory
+    const int lim = smem_limit < kJacobiSmemMax ? smem_limit : kJacobiSmemMax;
+    const int sm_dim = max_dim < lim ? max_dim : lim;
     const size_t smem = static_cast<size_t>(2) * sm_dim * sm_dim * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          2 * kJacobiSmemMax * kJacobiSmemMax * static_cast<int>(sizeof(double)));
     if (e != cudaSuccess) return e;
-    k_jacobi_batched<<<n_mats, 512, smem, st>>>(mats, vscratch, evals, mat_off, val_off, dims, status);
+    k_jacobi_batched<<<n_mats, 512, smem, st>>>(mats, vscratch, evals, mat_off, val_off, dims, sm_dim, status);
     return cudaGetLastError();
 }
 

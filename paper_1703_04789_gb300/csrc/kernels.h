@@ -65,9 +65,10 @@ cudaError_t launch_restart_coef(const double* c_new, const double* c_old, int m,
 // mats: concatenated row-major n_i x n_i matrices (overwritten by the eigenvector matrices,
 // columns = vectors, sorted by descending eigenvalue), evals: concatenated eigenvalues.
 // vscratch: same size as mats (used for matrices above the shared-memory limit of 112).
+// Matrices up to min(smem_limit, 112) run in shared memory.
 cudaError_t launch_jacobi_batched(double* mats, double* vscratch, double* evals, const int64_t* mat_off,
-                                  const int64_t* val_off, const int* dims, int n_mats, int max_dim, int* status,
-                                  cudaStream_t st);
+                                  const int64_t* val_off, const int* dims, int n_mats, int max_dim, int smem_limit,
+                                  int* status, cudaStream_t st);
 
 // Ordered truncation of singular values sqrt(max(evals, 0)) (one CTA): values within
 // tie_rtol * max of their sorted predecessor form a cluster ordered by (n, 2m, index);

@@ -27,7 +27,10 @@ using namespace spmps::eng;
 namespace {
 
 constexpr double kTieRtol = 1e-10;   // relative gap below which singular values are tied
-constexpr double kDropAbs = 1e-14;   // singular values below this are dropped (|x| = 1)
+// Singular values below this are dropped (|x| = 1, so the dropped weight per value is < 1e-14).
+// It sits above the noise floor of density-matrix eigenvalues in FP64 (~1e-16 absolute, i.e.
+// ~1e-8 in singular values), so numerically null directions are never kept.
+constexpr double kDropAbs = 1e-7;
 constexpr double kEpsMetric = 1e-12;
 constexpr double kClamp = 1e-4;
 
@@ -324,8 +327,7 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
                         sg.b = handle(0, xblock(la2, sb));
                         sg.b_rs = 1;
                         sg.b_cs = xl.width[la2];
-                        sg.alpha = 1.0;
-                        G.segs.push_back(sg);
+                                                G.segs.push_back(sg);
                     }
                     T.nseg = static_cast<int>(G.segs.size()) - T.seg0;
                     G.tasks.push_back(T);
@@ -354,8 +356,7 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
                         sg.b = handle(0, xblock(la, sb));
                         sg.b_rs = xl.width[la];
                         sg.b_cs = 1;
-                        sg.alpha = 1.0;
-                        G.segs.push_back(sg);
+                                                G.segs.push_back(sg);
                     }
                     T.nseg = static_cast<int>(G.segs.size()) - T.seg0;
                     G.tasks.push_back(T);
@@ -381,8 +382,15 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
     Slots S{};
     S.p[0] = x;
     S.p[1] = B.mats.as<double>();
-    CK(launch_gemm_f64(S, B.tasks.as<GemmTask>(), B.segs.as<GemmSeg>(), B.tiles.as<GemmTile>(), B.cmaps.as<int>(),
-                       static_cast<int>(G.tiles.size()), h->stream));
+    {
+        double fl = 0.0;
+        for (const GemmTask& T : G.tasks)
+            for (int q = 0; q < T.nseg; ++q) fl += 2.0 * T.M * T.N * G.segs[T.seg0 + q].K;
+        const int rec = h->profile ? prof_begin(h, h->stream, 0, fl) : -1;
+        CK(launch_gemm_f64(S, B.tasks.as<GemmTask>(), B.segs.as<GemmSeg>(), B.tiles.as<GemmTile>(), B.cmaps.as<int>(),
+                           static_cast<int>(G.tiles.size()), h->stream));
+        if (rec >= 0) prof_end(h, h->stream, rec);
+    }
     ++h->launches;
     // batched Jacobi and ordered truncation
     std::vector<int64_t> mo, vo;
@@ -408,7 +416,8 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
     CK(B.sval.ensure(std::max(2 * total, 1) * sizeof(double)));
     CK(cudaMemsetAsync(B.status.p, 0, sizeof(int), h->stream));
     CK(launch_jacobi_batched(B.mats.as<double>(), B.vscr.as<double>(), B.evals.as<double>(), B.mat_off.as<int64_t>(),
-                             B.val_off.as<int64_t>(), B.dims.as<int>(), nm, maxdim, B.status.as<int>(), h->stream));
+                             B.val_off.as<int64_t>(), B.dims.as<int>(), nm, maxdim, h->opt.jacobi_smem_max,
+                             B.status.as<int>(), h->stream));
     CK(launch_truncate(B.evals.as<double>(), B.val_off.as<int64_t>(), B.dims.as<int>(), B.ln.as<int>(), B.ltm.as<int>(),
                        nm, total, Dmax, kTieRtol, kDropAbs, B.keep.as<int>(), B.keep_total.as<int>(), B.disc.as<double>(),
                        B.sidx.as<int>(), B.sval.as<double>(), h->stream));
@@ -475,8 +484,7 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
                     sg.b = handle(0, xblock(la, s));
                     sg.b_rs = xl.width[la];
                     sg.b_cs = 1;
-                    sg.alpha = 1.0;
-                    W.segs.push_back(sg);
+                                        W.segs.push_back(sg);
                 }
                 T.nseg = static_cast<int>(W.segs.size()) - T.seg0;
                 W.tasks.push_back(T);
@@ -519,8 +527,7 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
                     sg.b = handle(1, M.mat_off + static_cast<int64_t>(M.col_start[c]) * M.dim);
                     sg.b_rs = M.dim;
                     sg.b_cs = 1;
-                    sg.alpha = 1.0;
-                    W.segs.push_back(sg);
+                                        W.segs.push_back(sg);
                 }
                 T.nseg = static_cast<int>(W.segs.size()) - T.seg0;
                 W.tasks.push_back(T);
@@ -565,8 +572,15 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
     S2.p[1] = B.mats.as<double>();
     S2.p[2] = A0->as<double>();
     S2.p[3] = A1->as<double>();
-    CK(launch_gemm_f64(S2, d_tasks.as<GemmTask>(), d_segs.as<GemmSeg>(), d_tiles.as<GemmTile>(), d_cmaps.as<int>(),
-                       static_cast<int>(W.tiles.size()), h->stream));
+    {
+        double fl = 0.0;
+        for (const GemmTask& T : W.tasks)
+            for (int q = 0; q < T.nseg; ++q) fl += 2.0 * T.M * T.N * W.segs[T.seg0 + q].K;
+        const int rec = h->profile ? prof_begin(h, h->stream, 0, fl) : -1;
+        CK(launch_gemm_f64(S2, d_tasks.as<GemmTask>(), d_segs.as<GemmSeg>(), d_tiles.as<GemmTile>(), d_cmaps.as<int>(),
+                           static_cast<int>(W.tiles.size()), h->stream));
+        if (rec >= 0) prof_end(h, h->stream, rec);
+    }
     CK(launch_copy_blocks(S2, d_copies.as<CopyBlock>(), static_cast<int>(copies.size()), h->stream));
     h->launches += 4;
     CK(cudaStreamSynchronize(h->stream));
@@ -600,7 +614,7 @@ spmps_status spmps_canonicalize(spmps_handle h) {
         CK(xb.ensure(std::max<int64_t>(n, 1) * sizeof(double)));
         st = spmps_two_site(h, k, xb.as<double>());
         if (st != SPMPS_OK) return st;
-        st = decimate(h, k, xb.as<double>(), 1 << 30, false, B, nullptr);
+        st = decimate(h, k, xb.as<double>(), h->D, false, B, nullptr);
         if (st != SPMPS_OK) return st;
     }
     invalidate_all(h);

@@ -438,12 +438,12 @@ def test_untruncated_decimation_reconstructs_and_is_canonical():
 
 
 def test_ordered_truncation_tie_rule():
-    vals = [0.5, 0.3, 0.3 + 1e-13, 0.3, 0.1, 1e-15]
+    vals = [0.5, 0.3, 0.3 + 1e-13, 0.3, 0.1, 1e-9]
     tags = [(2, 0, 0), (3, 1, 0), (3, -1, 0), (2, 0, 1), (1, 1, 0), (0, 0, 0)]
     keep = S.ordered_truncation(vals, tags, 3)
     # 0.5 first; then the tie cluster {0.3 x 3} ordered by (n, 2m, index): (2,0,1), (3,-1,0), (3,1,0)
     assert keep == [0, 3, 2]
-    assert S.ordered_truncation(vals, tags, 10) == [0, 3, 2, 1, 4]  # 1e-15 dropped
+    assert S.ordered_truncation(vals, tags, 10) == [0, 3, 2, 1, 4]  # 1e-9 < 1e-7 dropped
 
 
 @pytest.mark.parametrize("precond", ["diag", "metric"])
