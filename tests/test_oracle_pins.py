@@ -460,3 +460,53 @@ def test_davidson_matches_library_generalised_eigensolver(precond):
     assert res.converged
     assert abs(res.theta - ex) < 1e-10
     assert abs(res.x @ Nm @ res.x - 1.0) < 1e-10
+
+
+# ---- learned preconditioner (oracle MLP) ---------------------------------------------------
+
+def test_mlp_gradients_match_finite_differences():
+    from oracle import mlp
+    p = mlp.init_params(3)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((16, mlp.N_FEATURES))
+    t = rng.standard_normal(16)
+    loss, g = mlp.loss_and_grads(p, X, t)
+    for key, idx in (("W1", (1, 5)), ("b1", (7,)), ("W2", (3, 11)), ("b2", (2,)), ("w3", (9,)), ("b3", (0,))):
+        h = 1e-6
+        q = {k: v.copy() for k, v in p.items()}
+        q[key][idx] += h
+        lp, _ = mlp.loss_and_grads(q, X, t)
+        q[key][idx] -= 2 * h
+        lm, _ = mlp.loss_and_grads(q, X, t)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[key][idx]) < 1e-6 * max(1.0, abs(fd)), key
+
+
+def test_mlp_features_reduce_to_diagonal_preconditioner_direction():
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    n = 50
+    r, dh, dn = rng.standard_normal(n), rng.uniform(1, 2, n), rng.uniform(0.1, 0.5, n)
+    f = mlp.features(r, dh, dn, -0.3)
+    d = -r / (dh + 0.3 * dn)
+    assert np.allclose(f[:, 1], np.sqrt(n) * d / np.linalg.norm(d))
+    assert abs(np.linalg.norm(f[:, 0]) - np.sqrt(n)) < 1e-12
+
+
+def test_adam_matches_closed_form_first_step():
+    from oracle import mlp
+    p = {"a": np.array([1.0, -2.0])}
+    g = {"a": np.array([0.5, -4.0])}
+    st = {}
+    mlp.adam_step(p, g, st, lr=0.1)
+    # the first bias-corrected Adam step is lr * sign(g) (up to eps)
+    assert np.allclose(p["a"], [1.0 - 0.1, -2.0 + 0.1], atol=1e-7)
+
+
+def test_bf16_rounding_matches_known_values():
+    from oracle import mlp
+    # 1 + 2^-8 is exactly half-way between bf16 neighbours 1 and 1 + 2^-7: ties to even -> 1
+    assert mlp.to_bf16(np.float32(1.0 + 2.0 ** -8)) == 1.0
+    assert mlp.to_bf16(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6  # half-way, rounds to even (up)
+    assert mlp.to_bf16(np.float32(1.0 + 2.0 ** -7)) == 1.0 + 2.0 ** -7      # representable
+    assert mlp.to_bf16(np.float32(-3.0)) == -3.0
