@@ -52,7 +52,8 @@ typedef enum {
 typedef struct {
     int batched;        /* 1: one grouped launch per contraction phase over all beta points and
                            blocks (default); 0: one launch per beta point and phase          */
-    int precond;        /* Davidson preconditioner: 0 = diagonal (default), 1 = metric CG    */
+    int precond;        /* Davidson correction: 0 = diagonal (default), 1 = metric CG,
+                           2 = learned (spmps_mlp_*; the diagonal correction is its fallback) */
     int cg_steps;       /* CG steps on N_eff t = r for precond == 1 (default 5)               */
     double dav_tol_r;   /* Davidson residual norm tolerance (default 1e-6)                    */
     double dav_tol_theta; /* Davidson eigenvalue change tolerance (default 1e-10)             */
@@ -61,6 +62,11 @@ typedef struct {
     int device;         /* CUDA device ordinal (default 0)                                    */
     int jacobi_smem_max; /* decimation blocks up to this size are diagonalised in shared memory,
                             larger ones in global memory (default and maximum 112; 0 = default) */
+    int precision;      /* bulk H_eff x block products: 0 = FP64 (default), 1 = TF32, 2 = 3xTF32
+                           (tensor cores, FP32 accumulation).  N_eff x, environments, Davidson and
+                           decimation stay FP64; with 1 or 2 each Davidson solve converges first
+                           with reduced-precision actions, then refines with FP64 actions from
+                           that vector to the FP64 tolerance. */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -114,7 +120,8 @@ spmps_status spmps_x_layout(spmps_handle h, int site, int64_t* n_x, int* n_block
  * (Fig. spmpsOpt (b), (c)) with the environments of the current MPS, built on demand.
  * x, y, z are DEVICE pointers in the row-block layout (n_x doubles each, x read-only; y or z
  * may be NULL to skip that output).  stream is a cudaStream_t (NULL: the handle's stream);
- * the call is asynchronous with respect to the host except when environments must be built. */
+ * the call is asynchronous with respect to the host except when environments must be built.
+ * The H part uses the handle's precision option (FP64, TF32 or 3xTF32 block products); z is FP64. */
 spmps_status spmps_apply_heff(spmps_handle h, int site, const double* x, double* y, double* z,
                               void* stream);
 
@@ -201,10 +208,50 @@ spmps_status spmps_stream(spmps_handle h, void** stream);
  * enable != 0 switches it on and clears the counters; enable == 0 switches it off. */
 spmps_status spmps_profile(spmps_handle h, int enable);
 
-/* Counters of the profiler for kernel `kind` (0 = k_gemm_f64, 1 = k_comb_f64): launches, total
- * device time in ms, and the algorithmic flops those launches performed (same rule as
- * spmps_apply_flops).  Synchronises the handle's stream. */
+/* Counters of the profiler for `kind`: 0 = k_gemm_f64 launches, 1 = k_comb_f64 launches (their
+ * algorithmic flops, same rule as spmps_apply_flops), 2 = the Davidson Ritz step (k_ritz),
+ * 3 = the rest of each Davidson iteration outside the projected action (dots, gemv, residual,
+ * Gram-Schmidt), 4 = the decimation eigen-solve and truncation, 5 = host time spent building and
+ * uploading contraction plans (ms of host clock, launches = plans built).  Synchronises the
+ * handle's stream. */
 spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops);
+
+/* ---- Learned Davidson correction (no counterpart in the paper) ------------------------------
+ * A perceptron 4 -> 256 -> 256 -> 1 (ReLU) maps, per element i of the two-site vector, the features
+ *   ( sqrt(n) r_i/|r|, sqrt(n) d_i/|d|, dn_i, tanh((dh_i - theta dn_i)/(1+|theta|)) ),
+ *   d = -r / (dh - theta dn) clamped to |.| >= 1e-4 (the diagonal correction),
+ * to a correction t_i; dh, dn are the diagonals of H_eff and N_eff, r the residual.  Parameters
+ * are one float vector: W1 (4 x 256 row-major), b1 (256), W2 (256 x 256 row-major [in][out]),
+ * b2 (256), w3 (256), b3 (1): 67329 floats.  With precond = 2 the correction is evaluated with the
+ * 256 x 256 layer on the tensor cores (BF16 operands, FP32 accumulation). */
+
+/* Harvest training pairs during Davidson solves (any preconditioner): for each of the first 32
+ * iterations of a solve, features at samples_per_iteration evenly spaced elements, with the
+ * target sqrt(n) e_i/|e|, e = x* - alpha x_j the part of the converged vector x* not along the
+ * current Ritz vector x_j.  capacity = total pairs kept on the device; when enabling with a
+ * larger capacity the buffer grows and earlier pairs are cleared; disabling keeps the pairs. */
+spmps_status spmps_mlp_harvest(spmps_handle h, int enable, int samples_per_iteration, int64_t capacity);
+
+/* Number of harvested pairs; features (4 per pair) and targets (may be NULL) copied to the host. */
+spmps_status spmps_mlp_data(spmps_handle h, int64_t* count, float* features, float* targets);
+
+/* set != 0: load 67329 parameters from the host (layout above); set == 0: read them back. */
+spmps_status spmps_mlp_params(spmps_handle h, float* params, int set);
+
+/* Mean squared error of the network on a host batch (X: B x 4, T: B) and its gradients with
+ * respect to every parameter (FP32 forward and backward on the device). */
+spmps_status spmps_mlp_loss_grad(spmps_handle h, const float* X, const float* T, int B, double* loss, float* grads);
+
+/* `steps` Adam steps (lr, beta1 0.9, beta2 0.999) on minibatches of `batch` harvested pairs drawn
+ * with SplitMix64(seed, step, position); reinit != 0 (or no parameters yet) starts from He-normal
+ * weights drawn from the same generator.  Returns the first and last minibatch loss. */
+spmps_status spmps_mlp_train(spmps_handle h, int steps, int batch, double lr, uint64_t seed, int reinit,
+                             double* loss_first, double* loss_last);
+
+/* The network's correction for host vectors r, dh, dn (n each) and theta; tensor_cores != 0
+ * runs the BF16 tensor-core path used inside Davidson, 0 an FP32 reference path. */
+spmps_status spmps_mlp_infer(spmps_handle h, const double* r, const double* dh, const double* dn, double theta,
+                             int64_t n, double* t, int tensor_cores);
 
 /* Quadrature used by the handle: beta_g and c_g (n_beta each, host arrays). */
 spmps_status spmps_quadrature(spmps_handle h, double* beta, double* c);

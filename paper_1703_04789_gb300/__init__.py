@@ -38,7 +38,7 @@ class Options(C.Structure):
         ("batched", C.c_int), ("precond", C.c_int), ("cg_steps", C.c_int),
         ("dav_tol_r", C.c_double), ("dav_tol_theta", C.c_double),
         ("dav_max_sub", C.c_int), ("dav_max_iter", C.c_int), ("device", C.c_int),
-        ("jacobi_smem_max", C.c_int),
+        ("jacobi_smem_max", C.c_int), ("precision", C.c_int),
     ]
 
 
@@ -85,6 +85,12 @@ def load_library(path: str | None = None):
         "spmps_stream": (i, [H, P(C.c_void_p)]),
         "spmps_profile": (i, [H, i]),
         "spmps_kernel_stats": (i, [H, i, P(i64), P(d), P(d)]),
+        "spmps_mlp_harvest": (i, [H, i, i, i64]),
+        "spmps_mlp_data": (i, [H, P(i64), P(C.c_float), P(C.c_float)]),
+        "spmps_mlp_params": (i, [H, P(C.c_float), i]),
+        "spmps_mlp_loss_grad": (i, [H, P(C.c_float), P(C.c_float), i, P(d), P(C.c_float)]),
+        "spmps_mlp_train": (i, [H, i, i, d, C.c_uint64, i, P(d), P(d)]),
+        "spmps_mlp_infer": (i, [H, P(d), P(d), P(d), d, i64, P(d), i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -103,15 +109,16 @@ class Spmps:
 
     def __init__(self, K, N, twoM, twoS, n_beta, D, *, batched=True, precond="diag", cg_steps=5,
                  dav_tol_r=1e-6, dav_tol_theta=1e-10, dav_max_sub=20, dav_max_iter=200, device=0,
-                 jacobi_smem_max=0):
+                 jacobi_smem_max=0, precision="fp64"):
         self.lib = load_library()
         o = Options()
         self.lib.spmps_default_options(C.byref(o))
         o.batched = 1 if batched else 0
-        o.precond = {"diag": 0, "metric": 1}[precond]
+        o.precond = {"diag": 0, "metric": 1, "learned": 2}[precond]
         o.cg_steps, o.dav_tol_r, o.dav_tol_theta = cg_steps, dav_tol_r, dav_tol_theta
         o.dav_max_sub, o.dav_max_iter, o.device = dav_max_sub, dav_max_iter, device
         o.jacobi_smem_max = jacobi_smem_max
+        o.precision = {"fp64": 0, "tf32": 1, "3xtf32": 2}[precision]
         h = C.c_void_p()
         self._h = None
         self._check(self.lib.spmps_create(K, N, twoM, twoS, n_beta, D, C.byref(o), C.byref(h)), None)
@@ -321,6 +328,55 @@ class Spmps:
         fl = C.c_double()
         self._check(self.lib.spmps_kernel_stats(self._h, kind, C.byref(n), C.byref(ms), C.byref(fl)))
         return {"launches": n.value, "ms": ms.value, "flops": fl.value}
+
+    # ---- learned Davidson correction --------------------------------------------------------
+    def mlp_harvest(self, enable=True, samples_per_iteration=512, capacity=1 << 21):
+        """Harvest (features, target) pairs during Davidson solves; disabling keeps the pairs."""
+        self._check(self.lib.spmps_mlp_harvest(self._h, 1 if enable else 0, samples_per_iteration,
+                                               capacity if enable else 0))
+
+    def mlp_data(self):
+        n = C.c_int64()
+        self._check(self.lib.spmps_mlp_data(self._h, C.byref(n), None, None))
+        X = np.zeros((max(n.value, 1), 4), dtype=np.float32)
+        T = np.zeros(max(n.value, 1), dtype=np.float32)
+        self._check(self.lib.spmps_mlp_data(self._h, C.byref(n), X.ctypes.data_as(C.POINTER(C.c_float)),
+                                            T.ctypes.data_as(C.POINTER(C.c_float))))
+        return X[:n.value], T[:n.value]
+
+    def mlp_set_params(self, flat):
+        p = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self.lib.spmps_mlp_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), 1))
+
+    def mlp_get_params(self):
+        p = np.zeros(67329, dtype=np.float32)
+        self._check(self.lib.spmps_mlp_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), 0))
+        return p
+
+    def mlp_loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(67329, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self.lib.spmps_mlp_loss_grad(self._h, X.ctypes.data_as(C.POINTER(C.c_float)),
+                                                 T.ctypes.data_as(C.POINTER(C.c_float)), X.shape[0], C.byref(loss),
+                                                 g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def mlp_train(self, steps, batch=4096, lr=1e-3, seed=5, reinit=True):
+        a = C.c_double()
+        b = C.c_double()
+        self._check(self.lib.spmps_mlp_train(self._h, steps, batch, lr, seed, 1 if reinit else 0, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def mlp_infer(self, r, dh, dn, theta, tensor_cores=True):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        dh = np.ascontiguousarray(dh, dtype=np.float64)
+        dn = np.ascontiguousarray(dn, dtype=np.float64)
+        t = np.zeros_like(r)
+        self._check(self.lib.spmps_mlp_infer(self._h, _dptr(r), _dptr(dh), _dptr(dn), theta, r.shape[0], _dptr(t),
+                                             1 if tensor_cores else 0))
+        return t
 
     def quadrature(self):
         b = np.zeros(self.n_beta)

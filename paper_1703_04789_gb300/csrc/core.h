@@ -111,7 +111,10 @@ struct GemmSeg {
     int pad;
 };
 struct GemmTile {
-    int task, m0, n0, shape;  // 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32; 5..19 split-K tiles
+    int task;
+    int16_t m0, n0;  // first output row / column of the tile
+    int16_t tm, tn;  // tile extent (warp-block shape only)
+    int shape;       // 0 16x16, 1 4x64, 2 64x4, 3 32x8, 4 8x32 register tiles; 5 warp block
 };
 
 // dst (rows x cols, ld) = sum over terms of coef * src (rows x cols, ld_src).

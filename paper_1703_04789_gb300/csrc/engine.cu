@@ -10,6 +10,7 @@
 //   phase C: y    = sum_{g,u} T3[u] R_g[u]^T on the (N, M)-allowed output blocks only.
 // Environment updates use the same three phases with one site.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -137,11 +138,19 @@ bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why) {
                 return false;
         }
     }
-    for (const GemmTile& t : G.tiles)
-        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 19) {
+    for (const GemmTile& t : G.tiles) {
+        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 5) {
             *why = "bad tile";
             return false;
         }
+        const GemmTask& T = G.tasks[t.task];
+        if (t.m0 < 0 || t.n0 < 0 || t.m0 >= T.M || t.n0 >= T.N) { *why = "tile outside its task"; return false; }
+        if (t.shape == 5 && (t.tm < 1 || t.tn < 1 || t.tm > 32 || t.tn > 32 || t.tm * t.tn > 256 ||
+                             t.m0 + t.tm > T.M || t.n0 + t.tn > T.N)) {
+            *why = "bad warp-block tile";
+            return false;
+        }
+    }
     return true;
 }
 
@@ -168,6 +177,16 @@ bool validate_plan(const Plan& P, const int64_t* sizes, std::string* why) {
 // ---- plan upload and launch -------------------------------------------------------------------
 
 spmps_status plan_upload(spmps_t* h, Plan& P) {
+    const auto t0 = std::chrono::steady_clock::now();
+    struct Done {
+        spmps_t* h;
+        std::chrono::steady_clock::time_point t0;
+        ~Done() {
+            if (!h->profile) return;
+            h->prof_launches[5] += 1;
+            h->prof_ms[5] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+    } done{h, t0};
     P.A.add_tiles();
     P.C.add_tiles();
     CK(upload(P.d_tasksA, P.A.tasks, h->stream));
@@ -229,14 +248,30 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
         for (int r = a; r < b && r < static_cast<int>(f.size()); ++r) acc += f[r];
         return acc;
     };
+    // the H part (op 0) of a projected action may run on the tensor cores (precision 1 or 2)
+    const int prec = P.reduce_nx > 0 ? h->apply_precision : 0;
+    const int G = h->G;
+    auto gemm = [&](const DevMem& tasks, const DevMem& segs, const DevMem& tiles, const DevMem& cmaps,
+                    const std::vector<int>& rng, const std::vector<double>& fl, int a, int b) -> cudaError_t {
+        auto one = [&](int lo, int hi, int tf) -> cudaError_t {
+            if (hi <= lo) return cudaSuccess;
+            const int t0 = rng[lo], t1 = rng[hi];
+            ++h->launches;
+            const int rec = h->profile ? prof_begin(h, st, 0, range_flops(fl, lo, hi)) : -1;
+            cudaError_t e = tf ? launch_gemm_tf32(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
+                                                  cmaps.as<int>(), t1 - t0, tf == 2, st)
+                               : launch_gemm_f64(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
+                                                 cmaps.as<int>(), t1 - t0, st);
+            if (rec >= 0) prof_end(h, st, rec);
+            return e;
+        };
+        if (prec == 0) return one(a, b, 0);
+        cudaError_t e = one(a, std::min(b, G), prec);
+        if (e != cudaSuccess) return e;
+        return one(std::max(a, G), b, 0);
+    };
     auto runA = [&](int a, int b) -> cudaError_t {
-        const int t0 = P.tileA_rng[a], t1 = P.tileA_rng[b];
-        ++h->launches;
-        const int rec = h->profile ? prof_begin(h, st, 0, range_flops(P.flopsA_rng, a, b)) : -1;
-        cudaError_t e = launch_gemm_f64(S, P.d_tasksA.as<GemmTask>(), P.d_segsA.as<GemmSeg>(),
-                                        P.d_tilesA.as<GemmTile>() + t0, P.d_cmapsA.as<int>(), t1 - t0, st);
-        if (rec >= 0) prof_end(h, st, rec);
-        return e;
+        return gemm(P.d_tasksA, P.d_segsA, P.d_tilesA, P.d_cmapsA, P.tileA_rng, P.flopsA_rng, a, b);
     };
     auto runB = [&](int a, int b) -> cudaError_t {
         const int o0 = P.combB_rng[a], o1 = P.combB_rng[b];
@@ -247,13 +282,7 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
         return e;
     };
     auto runC = [&](int a, int b) -> cudaError_t {
-        const int t0 = P.tileC_rng[a], t1 = P.tileC_rng[b];
-        ++h->launches;
-        const int rec = h->profile ? prof_begin(h, st, 0, range_flops(P.flopsC_rng, a, b)) : -1;
-        cudaError_t e = launch_gemm_f64(S, P.d_tasksC.as<GemmTask>(), P.d_segsC.as<GemmSeg>(),
-                                        P.d_tilesC.as<GemmTile>() + t0, P.d_cmapsC.as<int>(), t1 - t0, st);
-        if (rec >= 0) prof_end(h, st, rec);
-        return e;
+        return gemm(P.d_tasksC, P.d_segsC, P.d_tilesC, P.d_cmapsC, P.tileC_rng, P.flopsC_rng, a, b);
     };
     if (batched) {
         CK(runA(r0, r1));
@@ -267,6 +296,13 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
         for (int r = r0; r < r1; ++r) CK(runB(r, r + 1));
         if (ev) CK(cudaEventRecord(ev[3], st));
         for (int r = r0; r < r1; ++r) CK(runC(r, r + 1));
+    }
+    if (P.reduce_nx > 0) {
+        // outputs of op: y (slot 1) from the partials in slot 8, z (slot 2) from slot 9
+        for (int op = r0 / G; op < (r1 + G - 1) / G && op < 2; ++op) {
+            CK(launch_sum_partials(S.p[8 + op], G, P.reduce_nx, S.p[1 + op], st));
+            ++h->launches;
+        }
     }
     if (ev) CK(cudaEventRecord(ev[4], st));
     return SPMPS_OK;
@@ -742,30 +778,32 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
             (void)dwm;
         }
     }
-    // phase C (all g for one output block in one task): y/z blocks of the (N, M) pattern
+    // phase C: one task per (N, M)-allowed output block and beta point, writing the partial sum
+    // over the channels u into the per-g slice of the partial buffer (slot 8 for y, 9 for z); a
+    // deterministic reduction over g (launch_sum_partials) produces y and z
+    const int64_t nx = xl.size;
     for (int op = 0; op < nops; ++op) {
         const MPO& m = h->ops.mpo[op];
         const int dwr = m.dw[k + 2];
-        const std::vector<int>& cnr = m.cn[k + 2];
         const double fc0 = P.C.flops;
-        P.tileC_rng[op * G] = static_cast<int>(P.C.tasks.size());
-        for (size_t la = 0; la < bl.labels.size(); ++la) {
-            const Label& La = bl.labels[la];
-            const int ga = La.group;
-            for (int s = 0; s < 16; ++s) {
-                const int lb = xl.seg_label[la * 16 + s];
-                if (lb < 0) continue;
-                const Label& Lb = br.labels[lb];
-                const int gb = Lb.group;
-                GemmTask T{};
-                T.c = handle(op == 0 ? 1 : 2, xl.row_off[la] + xl.seg_col[la * 16 + s]);
-                T.cmap = -1;
-                T.M = La.dim;
-                T.N = Lb.dim;
-                T.ldc = xl.width[la];
-                T.seg0 = static_cast<int>(P.C.segs.size());
-                for (int g = 0; g < G; ++g) {
-                    const int og = op * G + g;
+        for (int g = 0; g < G; ++g) {
+            const int og = op * G + g;
+            P.tileC_rng[og] = static_cast<int>(P.C.tasks.size());
+            for (size_t la = 0; la < bl.labels.size(); ++la) {
+                const Label& La = bl.labels[la];
+                const int ga = La.group;
+                for (int s = 0; s < 16; ++s) {
+                    const int lb = xl.seg_label[la * 16 + s];
+                    if (lb < 0) continue;
+                    const Label& Lb = br.labels[lb];
+                    const int gb = Lb.group;
+                    GemmTask T{};
+                    T.c = handle(8 + op, static_cast<int64_t>(g) * nx + xl.row_off[la] + xl.seg_col[la * 16 + s]);
+                    T.cmap = -1;
+                    T.M = La.dim;
+                    T.N = Lb.dim;
+                    T.ldc = xl.width[la];
+                    T.seg0 = static_cast<int>(P.C.segs.size());
                     for (int u = 0; u < dwr; ++u) {
                         const int64_t s3 = o3_all[og][u * ngl + ga];
                         if (s3 < 0) continue;
@@ -782,22 +820,17 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                         sg.b = handle(6, Re.base[og] + roff + static_cast<int64_t>(Lb.off - br.groups[gb].off) * K);
                         sg.b_rs = 1;
                         sg.b_cs = K;
-                                                P.C.segs.push_back(sg);
+                        P.C.segs.push_back(sg);
                         P.C.flops += 2.0 * T.M * T.N * K;
                     }
+                    T.nseg = static_cast<int>(P.C.segs.size()) - T.seg0;
+                    P.C.tasks.push_back(T);
                 }
-                T.nseg = static_cast<int>(P.C.segs.size()) - T.seg0;
-                P.C.tasks.push_back(T);
             }
         }
-        for (int g = 1; g <= G; ++g)
-            if (op * G + g <= nops * G) P.tileC_rng[op * G + g] = static_cast<int>(P.C.tasks.size());
         P.flops_op[op] += P.C.flops - fc0;
     }
-    // the output phase of op is one range: collapse per-g ranges so that range (op*G, op*G+G)
-    // covers it; per-g launches of phase C run it with the first g
-    for (int op = 0; op < nops; ++op)
-        for (int g = 1; g < G; ++g) P.tileC_rng[op * G + g] = P.tileC_rng[(op + 1) * G];
+    P.reduce_nx = nx;
     P.tileA_rng[nops * G] = static_cast<int>(P.A.tasks.size());
     P.combB_rng[nops * G] = static_cast<int>(P.B.outs.size());
     P.tileC_rng[nops * G] = static_cast<int>(P.C.tasks.size());
@@ -972,11 +1005,13 @@ spmps_status get_apply_plan(spmps_t* h, int k, Plan** out) {
             sz[4] = P->t2_size;
             sz[5] = h->Lenv[k].total;
             sz[6] = h->Renv[k + 2].total;
+            sz[8] = sz[9] = static_cast<int64_t>(h->G) * nx;
             std::string why;
             if (!validate_plan(*P, sz, &why)) return fail(h, SPMPS_ERR_CUDA, "internal plan check (apply): " + why);
         }
         st = plan_upload(h, *P);
         if (st != SPMPS_OK) return st;
+        CK(h->work3.ensure(std::max<int64_t>(1, 2 * static_cast<int64_t>(h->G) * P->reduce_nx) * sizeof(double)));
         h->apply_plans[k] = std::move(P);
     }
     *out = h->apply_plans[k].get();
@@ -996,6 +1031,8 @@ spmps_status do_apply(spmps_t* h, int k, const double* x, double* y, double* z, 
     S.p[4] = h->work2.as<double>();
     S.p[5] = h->Lenv[k].buf.as<double>();
     S.p[6] = h->Renv[k + 2].buf.as<double>();
+    S.p[8] = h->work3.as<double>();
+    S.p[9] = h->work3.as<double>() + static_cast<int64_t>(h->G) * P->reduce_nx;
     const int G = h->G;
     if (y && z) s = plan_run(h, *P, S, 0, 2 * G, st, ev);
     else if (y) s = plan_run(h, *P, S, 0, G, st, ev);
@@ -1100,6 +1137,7 @@ void spmps_default_options(spmps_options* o) {
     o->dav_max_iter = 200;
     o->device = 0;
     o->jacobi_smem_max = 0;
+    o->precision = 0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1122,6 +1160,8 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "jacobi_smem_max must be in [0, 112]");
     if (o.jacobi_smem_max == 0) o.jacobi_smem_max = 112;
+    if (o.precond < 0 || o.precond > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precond must be 0, 1 or 2");
+    if (o.precision < 0 || o.precision > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precision must be 0, 1 or 2");
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
     if (ce != cudaSuccess || ndev <= o.device)
@@ -1319,7 +1359,10 @@ spmps_status spmps_apply_heff(spmps_handle h, int site, const double* x, double*
         if (st != SPMPS_OK) return st;
         CK(cudaStreamSynchronize(h->stream));
     }
-    return do_apply(h, site, x, y, z, s);
+    h->apply_precision = h->opt.precision;
+    st = do_apply(h, site, x, y, z, s);
+    h->apply_precision = 0;
+    return st;
 }
 
 spmps_status spmps_apply_heff_timed(spmps_handle h, int site, const double* x, double* y, double* z, void* stream,
@@ -1383,8 +1426,10 @@ spmps_status spmps_apply_heff_host(spmps_handle h, int site, const double* x, do
     CK(h->ybuf.ensure(nb));
     CK(h->zbuf.ensure(nb));
     CK(cudaMemcpyAsync(h->xbuf.p, x, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->apply_precision = h->opt.precision;
     st = do_apply(h, site, h->xbuf.as<double>(), y ? h->ybuf.as<double>() : nullptr, z ? h->zbuf.as<double>() : nullptr,
                   h->stream);
+    h->apply_precision = 0;
     if (st != SPMPS_OK) return st;
     if (y) CK(cudaMemcpyAsync(y, h->ybuf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (z) CK(cudaMemcpyAsync(z, h->zbuf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1555,14 +1600,18 @@ spmps_status spmps_profile(spmps_handle h, int enable) {
     if (st != SPMPS_OK) return st;
     h->profile = enable != 0;
     if (enable) {
-        for (int k = 0; k < 2; ++k) { h->prof_launches[k] = 0; h->prof_ms[k] = 0.0; h->prof_flops[k] = 0.0; }
+        for (int k = 0; k < spmps_t::kProfKinds; ++k) {
+            h->prof_launches[k] = 0;
+            h->prof_ms[k] = 0.0;
+            h->prof_flops[k] = 0.0;
+        }
     }
     return SPMPS_OK;
 }
 
 spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops) {
     if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
-    if (kind < 0 || kind > 1) return fail(h, SPMPS_ERR_BAD_INPUT, "kind must be 0 or 1");
+    if (kind < 0 || kind >= spmps_t::kProfKinds) return fail(h, SPMPS_ERR_BAD_INPUT, "kind out of range");
     spmps_status st = prof_collect(h);
     if (st != SPMPS_OK) return st;
     if (launches) *launches = h->prof_launches[kind];

@@ -11,6 +11,7 @@
 #include "../../include/spmps.h"
 #include "core.h"
 #include "kernels.h"
+#include "mlp.h"
 
 namespace spmps {
 
@@ -76,6 +77,7 @@ struct Plan {
     std::vector<int> tileA_rng, tileC_rng, combB_rng;  // [op * G + g] .. [op * G + g + 1]
     std::vector<double> flopsA_rng, flopsB_rng, flopsC_rng;  // algorithmic flops per range
     int64_t t1_size = 0, t2_size = 0;
+    int64_t reduce_nx = 0;  // > 0: phase C writes per-beta partials of this length (slots 8, 9)
     double flops = 0.0;
     double flops_op[4] = {0, 0, 0, 0};
     DevMem d_tasksA, d_segsA, d_tilesA, d_cmapsA, d_outsB, d_termsB, d_tasksC, d_segsC, d_tilesC, d_cmapsC;
@@ -87,6 +89,20 @@ struct Plan {
 };
 
 }  // namespace spmps
+
+// State of the learned Davidson correction.
+struct MlpState {
+    spmps::DevMem params, grads, m, v, w2core, err;
+    spmps::DevMem X, T, Z1, H1, Z2, H2, dZ2, dZ1, dy, loss_part, loss;  // training step buffers
+    spmps::DevMem data_x, data_t;  // harvested set (features, targets)
+    int64_t count = 0, capacity = 0;
+    int batch = 0, step = 0;
+    bool ready = false;  // parameters present on the device
+    // harvesting
+    bool harvest = false;
+    int samples = 512, max_iters = 32;
+    spmps::DevMem h_idx, h_feat, h_x, h_norm, h_dots;  // per solve
+};
 
 struct spmps_t {
     int K = 0, N = 0, twoM = 0, twoS = 0, G = 0, D = 0;
@@ -104,9 +120,11 @@ struct spmps_t {
     int center = 0;
     std::vector<spmps::EnvStore> Lenv, Renv;  // per bond
     std::vector<std::unique_ptr<spmps::Plan>> apply_plans;  // per site
-    spmps::DevMem work1, work2, partial;
+    spmps::DevMem work1, work2, work3, partial;
     spmps::DevMem xbuf, ybuf, zbuf;  // host-API staging
-    int64_t launches = 0, applies = 0, dav_iters = 0;
+    MlpState mlp;
+    int apply_precision = 0;  // precision of the H part of projected actions issued now (0 = FP64)
+    int64_t launches = 0, applies = 0, dav_iters = 0, refine_iters = 0;
     double last_apply_flops = 0.0, last_discarded = 0.0, apply_flops_total = 0.0;
     // per-launch event profiler
     struct TimerRec {
@@ -116,8 +134,9 @@ struct spmps_t {
     };
     bool profile = false;
     std::vector<TimerRec> timers_live, timers_free;
-    int64_t prof_launches[2] = {0, 0};
-    double prof_ms[2] = {0.0, 0.0}, prof_flops[2] = {0.0, 0.0};
+    static constexpr int kProfKinds = 6;
+    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0};
+    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace spmps {

@@ -94,35 +94,47 @@ ColLayout make_col_layout(const Bond& right, int n0, int ns, int sign) {
 }
 
 void GemmPlan::add_tiles() {
-    // register-tiled shapes 0..4 (rows x cols per warp) and split-K shapes 5..19 (rows x cols)
+    // register-tiled shapes 0..4 (rows x cols per warp); shape 5 = warp block for long reductions
     static const int shp[5][2] = {{16, 16}, {4, 64}, {64, 4}, {32, 8}, {8, 32}};
-    static const int ksh[15][2] = {{8, 4}, {4, 8}, {4, 4}, {8, 2}, {2, 8}, {4, 2}, {2, 4}, {8, 1},
-                                   {1, 8}, {2, 2}, {4, 1}, {1, 4}, {2, 1}, {1, 2}, {1, 1}};
     tiles.clear();
     for (size_t t = 0; t < tasks.size(); ++t) {
         const GemmTask& T = tasks[t];
         int64_t ktot = 0;
         for (int q = 0; q < T.nseg; ++q) ktot += segs[T.seg0 + q].K;
-        const bool splitk = ktot >= 96 && static_cast<int64_t>(T.M) * T.N <= 1024;
-        int best = -1, bm = 0, bn = 0;
-        int64_t best_cost = -1;
-        if (splitk) {
-            // least padded outputs; ties to more outputs per warp (fewer reductions)
-            for (int s = 0; s < 15; ++s) {
-                const int64_t tm = ksh[s][0], tn = ksh[s][1];
-                const int64_t tiles_n = ((T.M + tm - 1) / tm) * ((T.N + tn - 1) / tn);
-                const int64_t cost = tiles_n * tm * tn * 64 + tiles_n;
-                if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = 5 + s; bm = ksh[s][0]; bn = ksh[s][1]; }
-            }
-        } else {
-            for (int s = 0; s < 5; ++s) {
-                const int64_t tm = shp[s][0], tn = shp[s][1];
-                const int64_t cost = ((T.M + tm - 1) / tm) * tm * ((T.N + tn - 1) / tn) * tn;
-                if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = s; bm = shp[s][0]; bn = shp[s][1]; }
-            }
+        if (ktot >= 64 && static_cast<int64_t>(T.M) * T.N <= 4096) {
+            const int tm = T.M < 32 ? T.M : 32;
+            int tn = 256 / tm;
+            if (tn > 32) tn = 32;
+            if (tn > T.N) tn = T.N;
+            for (int m0 = 0; m0 < T.M; m0 += tm)
+                for (int n0 = 0; n0 < T.N; n0 += tn) {
+                    GemmTile g{};
+                    g.task = static_cast<int>(t);
+                    g.m0 = static_cast<int16_t>(m0);
+                    g.n0 = static_cast<int16_t>(n0);
+                    g.tm = static_cast<int16_t>(T.M - m0 < tm ? T.M - m0 : tm);
+                    g.tn = static_cast<int16_t>(T.N - n0 < tn ? T.N - n0 : tn);
+                    g.shape = 5;
+                    tiles.push_back(g);
+                }
+            continue;
         }
-        for (int m0 = 0; m0 < T.M; m0 += bm)
-            for (int n0 = 0; n0 < T.N; n0 += bn) tiles.push_back(GemmTile{static_cast<int>(t), m0, n0, best});
+        int best = 0;
+        int64_t best_cost = -1;
+        for (int s = 0; s < 5; ++s) {
+            const int64_t tm = shp[s][0], tn = shp[s][1];
+            const int64_t cost = ((T.M + tm - 1) / tm) * tm * ((T.N + tn - 1) / tn) * tn;
+            if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = s; }
+        }
+        for (int m0 = 0; m0 < T.M; m0 += shp[best][0])
+            for (int n0 = 0; n0 < T.N; n0 += shp[best][1]) {
+                GemmTile g{};
+                g.task = static_cast<int>(t);
+                g.m0 = static_cast<int16_t>(m0);
+                g.n0 = static_cast<int16_t>(n0);
+                g.shape = best;
+                tiles.push_back(g);
+            }
     }
 }
 

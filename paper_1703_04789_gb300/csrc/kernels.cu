@@ -76,88 +76,108 @@ __device__ __forceinline__ void gemm_tile(const Slots& S, const GemmTask& T, con
     }
 }
 
-// Split-K tiles (shapes 5..18): MR x NC outputs per warp (MR, NC in {1,2,4,8}, MR*NC <= 32,
-// a power of two); lane l accumulates the k indices congruent to l mod 32 of every segment, then
-// a recursive-halving shuffle reduce-scatter over log2(MR*NC) lane bits and a butterfly over the
-// remaining bits leaves output (l >> (5 - log2(MR*NC))) on the lanes whose low bits are zero.
-template <int MR, int NC>
-__device__ __forceinline__ void gemm_tile_splitk(const Slots& S, const GemmTask& T, const GemmSeg* __restrict__ segs,
-                                                 const int* __restrict__ cmaps, int m0, int n0, int lane) {
-    constexpr int NOUT = MR * NC;
-    constexpr int P = NOUT == 1 ? 0 : NOUT == 2 ? 1 : NOUT == 4 ? 2 : NOUT == 8 ? 3 : NOUT == 16 ? 4 : 5;
-    double v[NOUT];
+// Warp-block tile (shape 5): one warp computes a whole tm x tn output block (tm, tn <= 32,
+// tm * tn <= 256) of a task with a long reduction.  K is staged in chunks of 16 through the
+// warp's shared-memory slice with coalesced loads (two rows of 16 k per warp load), then every lane accumulates
+// its flattened outputs o = lane + 32 q (q < NQ) from shared memory, so the operand rows are read
+// once per block and no FMA is spent on padding beyond the last partial row of 32 outputs.
+constexpr int kWbK = 16;                    // K chunk
+constexpr int kWbStride = kWbK + 1;         // padded row stride of the staged chunks
+constexpr int kWbWarpSmem = 2 * 32 * kWbStride;  // doubles per warp (A rows and B rows)
+
+template <int NQ>
+__device__ __forceinline__ void gemm_tile_wb(const Slots& S, const GemmTask& T, const GemmSeg* __restrict__ segs,
+                                             const int* __restrict__ cmaps, int m0, int n0, int tm, int tn, int lane,
+                                             double* __restrict__ sm) {
+    double* As = sm;
+    double* Bs = sm + 32 * kWbStride;
+    const int nout = tm * tn;
+    double v[NQ];
+    int oa[NQ], ob[NQ];
 #pragma unroll
-    for (int i = 0; i < NOUT; ++i) v[i] = 0.0;
-    const int mr = min(MR, T.M - m0), nc = min(NC, T.N - n0);
+    for (int q = 0; q < NQ; ++q) {
+        v[q] = 0.0;
+        const int o = lane + 32 * q;
+        const int oo = o < nout ? o : 0;
+        oa[q] = (oo / tn) * kWbStride;
+        ob[q] = (oo % tn) * kWbStride;
+    }
     for (int sgi = 0; sgi < T.nseg; ++sgi) {
         const GemmSeg sg = segs[T.seg0 + sgi];
         const double* __restrict__ A = resolve(S, sg.a) + static_cast<int64_t>(m0) * sg.a_rs;
         const double* __restrict__ B = resolve(S, sg.b) + static_cast<int64_t>(n0) * sg.b_cs;
-        for (int k = lane; k < sg.K; k += 32) {
-            double a[MR], b[NC];
+        const int kl = lane & 15, rl = lane >> 4;
+        for (int k0 = 0; k0 < sg.K; k0 += kWbK) {
+            const int kc = min(kWbK, sg.K - k0);
+            const bool kv = kl < kc;
+            const int64_t ka = static_cast<int64_t>(k0 + kl) * sg.a_cs;
+            const int64_t kb = static_cast<int64_t>(k0 + kl) * sg.b_rs;
+            for (int i = rl; i < tm; i += 2)
+                As[i * kWbStride + kl] = kv ? __ldg(A + static_cast<int64_t>(i) * sg.a_rs + ka) : 0.0;
+            for (int j = rl; j < tn; j += 2)
+                Bs[j * kWbStride + kl] = kv ? __ldg(B + kb + static_cast<int64_t>(j) * sg.b_cs) : 0.0;
+            __syncwarp();
+            for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
-            for (int i = 0; i < MR; ++i)
-                a[i] = i < mr ? __ldg(A + static_cast<int64_t>(i) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs) : 0.0;
-#pragma unroll
-            for (int j = 0; j < NC; ++j)
-                b[j] = j < nc ? __ldg(B + static_cast<int64_t>(k) * sg.b_rs + static_cast<int64_t>(j) * sg.b_cs) : 0.0;
-#pragma unroll
-            for (int i = 0; i < MR; ++i)
-#pragma unroll
-                for (int j = 0; j < NC; ++j) v[i * NC + j] = fma(a[i], b[j], v[i * NC + j]);
+                for (int q = 0; q < NQ; ++q) v[q] = fma(As[oa[q] + kk], Bs[ob[q] + kk], v[q]);
+            }
+            __syncwarp();
         }
     }
+    double* C = resolve(S, T.c);
+    const int* cm = T.cmap >= 0 ? cmaps + T.cmap : nullptr;
 #pragma unroll
-    for (int st = 0; st < P; ++st) {
-        const int half = NOUT >> (st + 1), bit = 16 >> st;
-        const bool up = (lane & bit) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const double send = up ? v[i] : v[i + half];
-            const double keep = up ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    for (int q = 0; q < NQ; ++q) {
+        const int o = lane + 32 * q;
+        if (o < nout) {
+            const int i = o / tn, j = o % tn;
+            const int64_t cc = cm ? cm[n0 + j] : n0 + j;
+            C[static_cast<int64_t>(m0 + i) * T.ldc + cc] = v[q];
         }
-    }
-#pragma unroll
-    for (int bit = 16 >> P; bit > 0; bit >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], bit);
-    if ((lane & ((1 << (5 - P)) - 1)) != 0) return;
-    const int o = lane >> (5 - P), i = o / NC, j = o - i * NC;
-    if (i < mr && j < nc) {
-        const int* cm = T.cmap >= 0 ? cmaps + T.cmap : nullptr;
-        const int64_t cc = cm ? cm[n0 + j] : n0 + j;
-        resolve(S, T.c)[static_cast<int64_t>(m0 + i) * T.ldc + cc] = v[0];
     }
 }
 
 __global__ void __launch_bounds__(128) k_gemm_f64(Slots S, const GemmTask* __restrict__ tasks,
                                                   const GemmSeg* __restrict__ segs, const GemmTile* __restrict__ tiles,
                                                   const int* __restrict__ cmaps, int n_tiles) {
+    __shared__ double wb_smem[4 * kWbWarpSmem];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_tiles) return;
     const GemmTile tl = tiles[warp];
     const GemmTask T = tasks[tl.task];
+    if (tl.shape == 5) {
+        double* sm = wb_smem + (threadIdx.x >> 5) * kWbWarpSmem;
+        const int nq = (tl.tm * tl.tn + 31) / 32;
+        switch (nq) {
+            case 1: gemm_tile_wb<1>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            case 2: gemm_tile_wb<2>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            case 3: gemm_tile_wb<3>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            case 4: gemm_tile_wb<4>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            case 5: gemm_tile_wb<5>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            case 6: gemm_tile_wb<6>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            case 7: gemm_tile_wb<7>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+            default: gemm_tile_wb<8>(S, T, segs, cmaps, tl.m0, tl.n0, tl.tm, tl.tn, lane, sm); break;
+        }
+        return;
+    }
     switch (tl.shape) {
         case 1: gemm_tile<4, 8, 1, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 2: gemm_tile<8, 4, 8, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 3: gemm_tile<8, 4, 4, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         case 4: gemm_tile<4, 8, 2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 5: gemm_tile_splitk<8, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 6: gemm_tile_splitk<4, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 7: gemm_tile_splitk<4, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 8: gemm_tile_splitk<8, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 9: gemm_tile_splitk<2, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 10: gemm_tile_splitk<4, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 11: gemm_tile_splitk<2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 12: gemm_tile_splitk<8, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 13: gemm_tile_splitk<1, 8>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 14: gemm_tile_splitk<2, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 15: gemm_tile_splitk<4, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 16: gemm_tile_splitk<1, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 17: gemm_tile_splitk<2, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 18: gemm_tile_splitk<1, 2>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
-        case 19: gemm_tile_splitk<1, 1>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
         default: gemm_tile<8, 4, 2, 4>(S, T, segs, cmaps, tl.m0, tl.n0, lane); break;
+    }
+}
+
+// ---- beta reduction of the output partials ------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ partial, int G, int64_t n,
+                                                      double* __restrict__ out) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double acc = 0.0;
+        for (int g = 0; g < G; ++g) acc += partial[g * n + i];
+        out[i] = acc;
     }
 }
 
@@ -343,6 +363,7 @@ __device__ int jacobi_cta(double* A, int lda, double* V, int ldv, int n, int max
     const int np = (n + 1) & ~1;  // players, even
     const int half = np / 2;
     int sweep = 0;
+    double off_prev = INFINITY;
     for (; sweep < max_sweeps; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int e = tid; e < n * n; e += nt) {
@@ -358,7 +379,11 @@ __device__ int jacobi_cta(double* A, int lda, double* V, int ldv, int n, int max
         __syncthreads();
         off = red_sh[33];
         tot = red_sh[34];
-        if (off <= 1e-30 * tot || off == 0.0) break;
+        // converged, or near convergence and at the rounding-noise floor (a sweep no longer reduces
+        // the off-diagonal norm: Jacobi converges quadratically until rounding noise dominates)
+        if (off <= 1e-28 * tot || off == 0.0 || (off <= 1e-20 * tot && off > 0.25 * off_prev)) break;
+        off_prev = off;
+        const double tiny = 1e-18 * sqrt(tot);
         for (int round = 0; round < np - 1; ++round) {
             for (int i = tid; i < half; i += nt) {
                 auto player = [&](int k) { return k == 0 ? 0 : 1 + ((k - 1 + round) % (np - 1)); };
@@ -367,12 +392,14 @@ __device__ int jacobi_cta(double* A, int lda, double* V, int ldv, int n, int max
                 double c = 1.0, s = 0.0;
                 if (q < n) {
                     const double apq = A[p * lda + q];
-                    if (apq != 0.0) {
+                    if (fabs(apq) > tiny) {
                         const double app = A[p * lda + p], aqq = A[q * lda + q];
                         const double theta = (aqq - app) / (2.0 * apq);
                         const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(t * t + 1.0);
                         s = t * c;
+                    } else {
+                        q = -1;  // negligible coupling: no rotation, no update
                     }
                 } else {
                     q = -1;
@@ -494,6 +521,229 @@ __global__ void __launch_bounds__(256) k_ritz(const double* __restrict__ h, cons
     }
 }
 
+// ---- incremental Ritz step (one warp) ---------------------------------------------------------
+// Keeps, across the iterations of one Davidson solve, an n-orthonormal coefficient basis X
+// (Y = V X has Y^T N Y = I), the projected matrix hp = X^T h X and the eigenvectors C of hp.
+// Adding basis vector v_m: classical Gram-Schmidt of e_m against X in the n inner product,
+// twice; the direction is kept when its n-norm^2 exceeds eps * max(diag n) (numerically null
+// directions of the metric are dropped, as in canonical orthogonalisation).  hp grows by one row
+// and column; its eigenproblem is re-solved by warp-level cyclic Jacobi started from the previous
+// eigenvectors, so only the new coupling has to be rotated away.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ int warp_jacobi(double* A, double* V, int n, int lane, int max_sweeps, double* cs, int* pq) {
+    constexpr int R = RitzState::kR;
+    for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e - i * n;
+        V[i * R + j] = i == j ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    if (n <= 1) return 0;
+    const int np = (n + 1) & ~1, half = np / 2;
+    int sweep = 0;
+    double off_prev = INFINITY;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int e = lane; e < n * n; e += 32) {
+            const int i = e / n, j = e - i * n;
+            const double v = A[i * R + j];
+            tot += v * v;
+            if (i != j) off += v * v;
+        }
+        off = warp_sum(off);
+        tot = warp_sum(tot);
+        // converged, or near convergence and at the rounding-noise floor
+        if (off <= 1e-28 * tot || off == 0.0 || (off <= 1e-20 * tot && off > 0.25 * off_prev)) break;
+        off_prev = off;
+        const double tiny = 1e-18 * sqrt(tot);
+        for (int round = 0; round < np - 1; ++round) {
+            if (lane < half) {
+                auto player = [&](int k) { return k == 0 ? 0 : 1 + ((k - 1 + round) % (np - 1)); };
+                int p = player(lane), q = player(np - 1 - lane);
+                if (p > q) { const int t = p; p = q; q = t; }
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    const double apq = A[p * R + q];
+                    if (fabs(apq) > tiny) {
+                        const double theta = (A[q * R + q] - A[p * R + p]) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    } else {
+                        q = -1;
+                    }
+                } else {
+                    q = -1;
+                }
+                pq[2 * lane] = p;
+                pq[2 * lane + 1] = q;
+                cs[2 * lane] = c;
+                cs[2 * lane + 1] = s;
+            }
+            __syncwarp();
+            for (int e = lane; e < half * n; e += 32) {
+                const int i = e / n, j = e - i * n;
+                const int p = pq[2 * i], q = pq[2 * i + 1];
+                if (q < 0) continue;
+                const double c = cs[2 * i], s = cs[2 * i + 1];
+                const double ap = A[p * R + j], aq = A[q * R + j];
+                A[p * R + j] = c * ap - s * aq;
+                A[q * R + j] = s * ap + c * aq;
+            }
+            __syncwarp();
+            for (int e = lane; e < half * n; e += 32) {
+                const int i = e / n, j = e - i * n;
+                const int p = pq[2 * i], q = pq[2 * i + 1];
+                if (q < 0) continue;
+                const double c = cs[2 * i], s = cs[2 * i + 1];
+                const double ap = A[j * R + p], aq = A[j * R + q];
+                A[j * R + p] = c * ap - s * aq;
+                A[j * R + q] = s * ap + c * aq;
+                const double vp = V[j * R + p], vq = V[j * R + q];
+                V[j * R + p] = c * vp - s * vq;
+                V[j * R + q] = s * vp + c * vq;
+            }
+            __syncwarp();
+        }
+    }
+    return sweep;
+}
+
+__global__ void __launch_bounds__(32) k_ritz_inc(const double* __restrict__ h, const double* __restrict__ nm, int ldm,
+                                                 int m, int reset, double eps, RitzState* __restrict__ st,
+                                                 double* __restrict__ coef, double* __restrict__ scal) {
+    constexpr int R = RitzState::kR;
+    extern __shared__ double rs_smem[];
+    double* X = rs_smem;           // n-orthonormal coefficient basis, X[i + j*R]
+    double* HP = X + R * R;        // X^T h X
+    double* CC = HP + R * R;       // previous eigenvectors of HP (columns)
+    double* A = CC + R * R;
+    double* T = A + R * R;
+    double* NS = T + R * R;        // n, full symmetric, NS[i*R + j]
+    double* HS = NS + R * R;       // h, full symmetric
+    __shared__ double cs[R + 2];
+    __shared__ int pq[R + 2];
+    const int lane = threadIdx.x;
+    int k = 0, m0 = 0, kc = 0;
+    if (!reset) {
+        k = st->k;
+        m0 = st->m;
+        kc = st->kc;
+        for (int e = lane; e < R * R; e += 32) {
+            X[e] = st->X[e];
+            HP[e] = st->hp[e];
+            CC[e] = st->C[e];
+        }
+    }
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - i * m;
+        const int hi = i > j ? i : j, lo = i > j ? j : i;
+        NS[i * R + j] = nm[hi * ldm + lo];
+        HS[i * R + j] = h[hi * ldm + lo];
+    }
+    __syncwarp();
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) dmax = fmax(dmax, NS[i * R + i]);
+    for (int col = m0; col < m; ++col) {
+        // y = e_col - X (X^T n y), twice, in the n inner product (lane i holds y_i, i <= col)
+        double y = lane == col ? 1.0 : 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            double ny = 0.0;
+            for (int l = 0; l <= col; ++l) {
+                const double yl = __shfl_sync(0xffffffffu, y, l);
+                if (lane <= col) ny = fma(NS[lane * R + l], yl, ny);
+            }
+            double corr = 0.0;
+            for (int j = 0; j < k; ++j) {
+                const double cj = warp_sum(lane <= col ? X[lane + j * R] * ny : 0.0);
+                if (lane <= col) corr = fma(X[lane + j * R], cj, corr);
+            }
+            y -= corr;
+        }
+        double ny = 0.0;
+        for (int l = 0; l <= col; ++l) {
+            const double yl = __shfl_sync(0xffffffffu, y, l);
+            if (lane <= col) ny = fma(NS[lane * R + l], yl, ny);
+        }
+        const double nu2 = warp_sum(lane <= col ? y * ny : 0.0);
+        if (nu2 > eps * dmax && nu2 > 0.0) {
+            const double inv = 1.0 / sqrt(nu2);
+            X[lane + k * R] = lane <= col ? y * inv : 0.0;
+            __syncwarp();
+            double hx = 0.0;
+            for (int l = 0; l <= col; ++l)
+                if (lane <= col) hx = fma(HS[lane * R + l], X[l + k * R], hx);
+            for (int j = 0; j <= k; ++j) {
+                const double v = warp_sum(lane <= col ? X[lane + j * R] * hx : 0.0);
+                if (lane == 0) { HP[j * R + k] = v; HP[k * R + j] = v; }
+            }
+            ++k;
+        }
+        __syncwarp();
+    }
+    // W = previous eigenvectors padded with the identity (in T), A = W^T HP W
+    for (int e = lane; e < k * k; e += 32) {
+        const int i = e / k, j = e - i * k;
+        T[i * R + j] = (i < kc && j < kc) ? CC[i * R + j] : (i == j ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    for (int e = lane; e < k * k; e += 32) {  // A = HP W
+        const int i = e / k, j = e - i * k;
+        double acc = 0.0;
+        for (int l = 0; l < k; ++l) acc = fma(HP[i * R + l], T[l * R + j], acc);
+        A[i * R + j] = acc;
+    }
+    __syncwarp();
+    for (int e = lane; e < k * k; e += 32) {  // CC = W^T (HP W)  (CC is free: W holds the old C)
+        const int i = e / k, j = e - i * k;
+        double acc = 0.0;
+        for (int l = 0; l < k; ++l) acc = fma(T[l * R + i], A[l * R + j], acc);
+        CC[i * R + j] = acc;
+    }
+    __syncwarp();
+    for (int e = lane; e < k * k; e += 32) {  // A = symmetrised W^T HP W
+        const int i = e / k, j = e - i * k;
+        A[i * R + j] = 0.5 * (CC[i * R + j] + CC[j * R + i]);
+    }
+    __syncwarp();
+    warp_jacobi(A, CC, k, lane, 40, cs, pq);  // CC = rotations
+    // new eigenvectors W * rotations, into NS (free now), then back to CC
+    for (int e = lane; e < k * k; e += 32) {
+        const int i = e / k, j = e - i * k;
+        double acc = 0.0;
+        for (int l = 0; l < k; ++l) acc = fma(T[i * R + l], CC[l * R + j], acc);
+        NS[i * R + j] = acc;
+    }
+    __syncwarp();
+    int jmin = 0;
+    for (int i = 1; i < k; ++i)
+        if (A[i * R + i] < A[jmin * R + jmin]) jmin = i;
+    for (int e = lane; e < R * R; e += 32) {
+        const int i = e / R, j = e - i * R;
+        const double c = (i < k && j < k) ? NS[i * R + j] : 0.0;
+        CC[e] = c;
+        st->C[e] = c;
+        st->X[e] = X[e];
+        st->hp[e] = HP[e];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        st->k = k;
+        st->m = m;
+        st->kc = k;
+        scal[0] = k > 0 ? A[jmin * R + jmin] : 0.0;
+        scal[1] = static_cast<double>(k);
+    }
+    if (lane < m) {
+        double acc = 0.0;
+        for (int j = 0; j < k; ++j) acc = fma(X[lane + j * R], CC[j * R + jmin], acc);
+        coef[lane] = k > 0 ? acc : 0.0;
+    }
+}
+
 // Orthonormal restart coefficients from [c_new, c_old] (Gram-Schmidt, twice).
 __global__ void k_restart_coef(const double* __restrict__ cn, const double* __restrict__ co, int m,
                                double* __restrict__ Q, double* __restrict__ out) {
@@ -517,6 +767,8 @@ __global__ void k_restart_coef(const double* __restrict__ cn, const double* __re
     if (nb > 1e-10) {
         k = 2;
         for (int i = 0; i < m; ++i) Q[m + i] = b[i] / nb;
+    } else {
+        for (int i = 0; i < m; ++i) Q[m + i] = 0.0;  // a zero second column (dropped downstream)
     }
     out[0] = k;
     // coefficients of the current Ritz vector in the rotated basis: Q^T c_new
@@ -553,7 +805,7 @@ __global__ void __launch_bounds__(512) k_jacobi_batched(double* __restrict__ mat
     }
     __syncthreads();
     const int sweeps = jacobi_cta(A, n, V, n, n, 60, cs_sh, pq_sh, red_sh);
-    if (threadIdx.x == 0 && sweeps >= 60) atomicExch(status, 1);
+    if (threadIdx.x == 0 && sweeps >= 60) atomicExch(status, 1);  // cap reached (not at the noise floor)
     for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = A[i * n + i];
     __syncthreads();
     // eigenpairs sorted by descending eigenvalue (rank sort, ties by index)
@@ -692,6 +944,12 @@ cudaError_t launch_gemm_f64(const Slots& slots, const GemmTask* tasks, const Gem
     return cudaGetLastError();
 }
 
+cudaError_t launch_sum_partials(const double* partial, int G, int64_t n, double* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_sum_partials<<<grid_for(n, 256, 4096), 256, 0, st>>>(partial, G, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_comb_f64(const Slots& slots, const CombOut* outs, const CombTerm* terms, int n_outs,
                             cudaStream_t st) {
     if (n_outs <= 0) return cudaSuccess;
@@ -734,6 +992,22 @@ cudaError_t launch_ritz(const double* h, const double* nmat, int ldm, int m, dou
                         double* scal, cudaStream_t st) {
     if (m > kRitzMax) return cudaErrorInvalidValue;
     k_ritz<<<1, 256, 0, st>>>(h, nmat, ldm, m, eps_metric, coef, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ritz_inc(const double* h, const double* nmat, int ldm, int m, int reset, double eps_metric,
+                            RitzState* state, double* coef, double* scal, cudaStream_t st) {
+    if (m > RitzState::kR) return cudaErrorInvalidValue;
+    constexpr int smem = 7 * RitzState::kR * RitzState::kR * static_cast<int>(sizeof(double));
+    static int attr_device = -1;  // the attribute is per device; set it once per device in use
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_ritz_inc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_device = dev;
+    }
+    k_ritz_inc<<<1, 32, smem, st>>>(h, nmat, ldm, m, reset, eps_metric, state, coef, scal);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,14 @@ namespace spmps {
 cudaError_t launch_gemm_f64(const Slots& slots, const GemmTask* tasks, const GemmSeg* segs,
                             const GemmTile* tiles, const int* cmaps, int n_tiles, cudaStream_t st);
 
+// out[i] = sum_{g < G} partial[g * n + i] (fixed order).
+cudaError_t launch_sum_partials(const double* partial, int G, int64_t n, double* out, cudaStream_t st);
+
+// Same task lists on the tensor cores (m16n8k8 TF32, FP32 accumulation, FP64 in and out);
+// split3 != 0 uses the 3xTF32 split (hi*hi + hi*lo + lo*hi).
+cudaError_t launch_gemm_tf32(const Slots& slots, const GemmTask* tasks, const GemmSeg* segs, const GemmTile* tiles,
+                             const int* cmaps, int n_tiles, int split3, cudaStream_t st);
+
 // Linear combination of equally shaped blocks (the MPO-leg contraction).
 cudaError_t launch_comb_f64(const Slots& slots, const CombOut* outs, const CombTerm* terms, int n_outs,
                             cudaStream_t st);
@@ -39,6 +47,18 @@ cudaError_t launch_basis_rotate(const double* src, int64_t ld, int m, const doub
 // scal[0] = theta, scal[1] = number of kept metric directions (0 = singular).
 cudaError_t launch_ritz(const double* h, const double* nmat, int ldm, int m, double eps_metric, double* coef,
                         double* scal, cudaStream_t st);
+
+// Incremental Ritz step (one warp): state kept across iterations of one solve; reset != 0
+// rebuilds it from the m stored columns.  Same outputs as launch_ritz.
+struct RitzState {
+    static constexpr int kR = 32;
+    double X[kR * kR];   // n-orthonormal coefficient basis, X[i + j*kR]
+    double hp[kR * kR];  // X^T h X
+    double C[kR * kR];   // eigenvectors of hp (columns)
+    int k, m, kc, pad;
+};
+cudaError_t launch_ritz_inc(const double* h, const double* nmat, int ldm, int m, int reset, double eps_metric,
+                            RitzState* state, double* coef, double* scal, cudaStream_t st);
 
 // r = hx - theta * nx, t = preconditioned correction, scal[2] = ||r||^2.
 cudaError_t launch_residual_diag(const double* hx, const double* nx, const double* dh, const double* dn,

@@ -62,7 +62,8 @@ extern "C" spmps_status spmps_apply_heff_noalloc(spmps_handle h, int site, const
     if (!P || !P->ready || !h->Lenv[site].valid || !h->Renv[site + 2].valid)
         return fail(h, SPMPS_ERR_STATE,
                     "no contraction plan for this site: call spmps_apply_heff once for it first (that call allocates)");
-    const size_t need = static_cast<size_t>(P->t1_size) + static_cast<size_t>(P->t2_size);
+    const size_t need = static_cast<size_t>(P->t1_size) + static_cast<size_t>(P->t2_size) +
+                        2 * static_cast<size_t>(h->G) * static_cast<size_t>(P->reduce_nx) + 64;
     if (need > kNoAllocScratchDoubles)
         return fail(h, SPMPS_ERR_BAD_INPUT, "intermediates need " + std::to_string(need) +
                                                 " doubles, above the fixed scratch of " +
@@ -79,7 +80,9 @@ extern "C" spmps_status spmps_apply_heff_noalloc(spmps_handle h, int site, const
     S.p[2] = z;
     S.p[3] = base;
     S.p[4] = base + ((P->t1_size + 31) / 32) * 32;
-    if (static_cast<size_t>(S.p[4] - base) + static_cast<size_t>(P->t2_size) > kNoAllocScratchDoubles)
+    S.p[8] = S.p[4] + ((P->t2_size + 31) / 32) * 32;
+    S.p[9] = S.p[8] + static_cast<int64_t>(h->G) * P->reduce_nx;
+    if (static_cast<size_t>(S.p[9] - base) + static_cast<size_t>(h->G) * P->reduce_nx > kNoAllocScratchDoubles)
         return fail(h, SPMPS_ERR_BAD_INPUT, "intermediates do not fit the fixed scratch");
     S.p[5] = h->Lenv[site].buf.as<double>();
     S.p[6] = h->Renv[site + 2].buf.as<double>();

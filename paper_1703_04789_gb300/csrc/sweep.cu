@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <map>
+#include <vector>
 
 #include "engine.h"
 
@@ -44,7 +45,7 @@ int64_t x_size(spmps_t* h, int k) { return make_row_block_layout(h->bonds[k], h-
 
 // Device work buffers of the Davidson solver.
 struct DavBuffers {
-    DevMem V, HV, NV, hm, nm, coef, coef_prev, scal, x, hx, nx, r, t, dh, dn, Q, tmp, cg_p, cg_ap, cg_res, dot;
+    DevMem V, HV, NV, hm, nm, coef, coef_prev, scal, x, hx, nx, r, t, dh, dn, Q, tmp, cg_p, cg_ap, cg_res, dot, ritz;
 };
 
 spmps_status ensure_dav(spmps_t* h, DavBuffers& B, int64_t n, int ms) {
@@ -61,6 +62,7 @@ spmps_status ensure_dav(spmps_t* h, DavBuffers& B, int64_t n, int ms) {
     CK(B.Q.ensure(sizeof(double) * 64 * 2));
     CK(B.scal.ensure(sizeof(double) * 16));
     CK(B.dot.ensure(sizeof(double) * 64));
+    CK(B.ritz.ensure(sizeof(RitzState)));
     return SPMPS_OK;
 }
 
@@ -118,8 +120,35 @@ spmps_status metric_cg(spmps_t* h, int k, DavBuffers& B, int64_t n, const double
 }
 
 // Lowest generalised eigenpair at sites (k, k+1), starting from the device vector x0 (n).
-// On return B.x holds x with x^T N x = 1.
+// On return B.x holds x with x^T N x = 1.  tol_r / tol_theta / cap are this stage's criteria.
+spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out, double tol_r,
+                            double tol_theta, int cap);
+
 spmps_status davidson(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out) {
+    if (h->opt.precision == 0) {
+        h->apply_precision = 0;
+        return davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter);
+    }
+    // reduced-precision stage (tensor-core H_eff x), then FP64 refinement from its vector
+    const double tol1 = h->opt.precision == 1 ? 1e-3 : 1e-5;
+    h->apply_precision = h->opt.precision;
+    DavidsonOut o1;
+    spmps_status st = davidson_stage(h, k, x0, B, &o1, std::max(tol1, h->opt.dav_tol_r), 1e-7, h->opt.dav_max_iter);
+    h->apply_precision = 0;
+    if (st != SPMPS_OK) return st;
+    DevMem xs;
+    const int64_t n = x_size(h, k);
+    CK(xs.ensure(std::max<int64_t>(n, 1) * sizeof(double)));
+    CK(cudaMemcpyAsync(xs.p, B.x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    const int64_t it0 = h->dav_iters;
+    st = davidson_stage(h, k, xs.as<double>(), B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter);
+    h->refine_iters += h->dav_iters - it0;
+    out->iters += o1.iters;
+    return st;
+}
+
+spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out, double tol_r,
+                            double tol_theta, int cap) {
     const int64_t n = x_size(h, k);
     const int ms = h->opt.dav_max_sub;
     spmps_status st = ensure_dav(h, B, n, ms);
@@ -147,83 +176,166 @@ spmps_status davidson(spmps_t* h, int k, const double* x0, DavBuffers& B, Davids
     st = subspace_column(h, B, n, ms, 0);
     if (st != SPMPS_OK) return st;
     int m = 1;
+    int reset = 1;  // rebuild the incremental Ritz state from the stored columns
     double theta_prev = INFINITY;
+    // harvesting of (features, error direction) pairs for the learned correction
+    MlpState& ML = h->mlp;
+    const bool harvest = ML.harvest && ML.count < ML.capacity;
+    const int hs = harvest ? static_cast<int>(std::min<int64_t>(ML.samples, n)) : 0;
+    int stored = 0;
+    if (harvest) {
+        std::vector<int64_t> idx(hs);
+        for (int q = 0; q < hs; ++q) idx[q] = (static_cast<int64_t>(q) * n) / hs;
+        CK(upload(ML.h_idx, idx, h->stream));
+        CK(ML.h_feat.ensure(static_cast<size_t>(ML.max_iters) * hs * mlp::N_FEATURES * sizeof(float)));
+        CK(ML.h_x.ensure(static_cast<size_t>(ML.max_iters) * n * sizeof(double)));
+        CK(ML.h_norm.ensure(64 * sizeof(double)));
+        CK(ML.h_dots.ensure(64 * sizeof(double)));
+    }
+    const bool learned = h->opt.precond == 2 && ML.ready;
+    if (learned) CK(ML.err.ensure(sizeof(int)));
+    auto finish_harvest = [&]() -> spmps_status {
+        if (!harvest || stored == 0) return SPMPS_OK;
+        const int64_t room = ML.capacity - ML.count;
+        const int use = static_cast<int>(std::min<int64_t>(stored, room / std::max(hs, 1)));
+        if (use <= 0) return SPMPS_OK;
+        CK(launch_multidot(ML.h_x.as<double>(), n, use, B.x.as<double>(), n, ML.h_dots.as<double>(),
+                           h->partial.as<double>(), h->stream));
+        CK(launch_norm2(B.x.as<double>(), n, ML.h_dots.as<double>() + 32, h->partial.as<double>(), h->stream));
+        CK(mlp::targets(ML.h_x.as<double>(), B.x.as<double>(), ML.h_dots.as<double>(), ML.h_norm.as<double>(),
+                        ML.h_dots.as<double>() + 32, ML.h_idx.as<int64_t>(), hs, use, n,
+                        ML.data_t.as<float>() + ML.count, h->stream));
+        CK(cudaMemcpyAsync(ML.data_x.as<float>() + ML.count * mlp::N_FEATURES, ML.h_feat.p,
+                           static_cast<size_t>(use) * hs * mlp::N_FEATURES * sizeof(float), cudaMemcpyDeviceToDevice,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->launches += 5;
+        ML.count += static_cast<int64_t>(use) * hs;
+        return SPMPS_OK;
+    };
     double host[4];
     out->converged = false;
-    for (int it = 1; it <= h->opt.dav_max_iter; ++it) {
-        CK(launch_ritz(B.hm.as<double>(), B.nm.as<double>(), ms, m, kEpsMetric, B.coef.as<double>(), sc, h->stream));
+    for (int it = 1; it <= cap; ++it) {
+        int rec = h->profile ? prof_begin(h, h->stream, 2, 0.0) : -1;
+        CK(launch_ritz_inc(B.hm.as<double>(), B.nm.as<double>(), ms, m, reset, kEpsMetric, B.ritz.as<RitzState>(),
+                           B.coef.as<double>(), sc, h->stream));
+        if (rec >= 0) prof_end(h, h->stream, rec);
+        reset = 0;
+        rec = h->profile ? prof_begin(h, h->stream, 3, 0.0) : -1;
         CK(launch_gemv(V, n, m, B.coef.as<double>(), n, B.x.as<double>(), 0, h->stream));
         CK(launch_gemv(B.HV.as<double>(), n, m, B.coef.as<double>(), n, B.hx.as<double>(), 0, h->stream));
         CK(launch_gemv(B.NV.as<double>(), n, m, B.coef.as<double>(), n, B.nx.as<double>(), 0, h->stream));
         CK(launch_residual_diag(B.hx.as<double>(), B.nx.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, kClamp,
                                 n, B.r.as<double>(), B.t.as<double>(), sc + 2, h->partial.as<double>(), h->stream));
         h->launches += 7;
-        CK(cudaMemcpyAsync(host, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (rec >= 0) prof_end(h, h->stream, rec);
+        if (h->opt.precond == 1) {
+            st = metric_cg(h, k, B, n, B.r.as<double>(), B.t.as<double>());
+            if (st != SPMPS_OK) return st;
+        }
+        if (harvest || learned) {
+            // |d|^2 of the diagonal correction (sc[7]) for the features
+            CK(launch_norm2(B.t.as<double>(), n, sc + 7, h->partial.as<double>(), h->stream));
+            h->launches += 2;
+        }
+        if (harvest && stored < ML.max_iters) {
+            CK(mlp::features(B.r.as<double>(), B.t.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, sc + 2,
+                             sc + 7, n, ML.h_idx.as<int64_t>(), hs,
+                             ML.h_feat.as<float>() + static_cast<size_t>(stored) * hs * mlp::N_FEATURES, h->stream));
+            CK(cudaMemcpyAsync(ML.h_x.as<double>() + static_cast<int64_t>(stored) * n, B.x.p, n * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->stream));
+            CK(launch_norm2(B.x.as<double>(), n, ML.h_norm.as<double>() + stored, h->partial.as<double>(), h->stream));
+            h->launches += 3;
+            ++stored;
+        }
+        const double* tsrc = B.t.as<double>();  // the correction to append: diagonal, CG, or learned
+        if (learned) {
+            CK(cudaMemsetAsync(ML.err.p, 0, sizeof(int), h->stream));
+            CK(mlp::infer_tc(B.r.as<double>(), B.t.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, sc + 2,
+                             sc + 7, n, ML.w2core.as<__nv_bfloat16>(), ML.params.as<float>(), B.cg_p.as<double>(),
+                             ML.err.as<int>(), h->stream));
+            ++h->launches;
+            tsrc = B.cg_p.as<double>();
+        }
+        rec = h->profile ? prof_begin(h, h->stream, 3, 0.0) : -1;
+        if (m == ms) {
+            // thick restart on [x, previous x]; a second column that is (nearly) parallel to the
+            // first comes back as zero and is dropped by the n-orthonormalisation
+            CK(launch_restart_coef(B.coef.as<double>(), B.coef_prev.as<double>(), m, B.Q.as<double>(), sc + 4, h->stream));
+            for (DevMem* buf : {&B.V, &B.HV, &B.NV}) {
+                CK(launch_basis_rotate(buf->as<double>(), n, m, B.Q.as<double>(), m, 2, n, B.tmp.as<double>(), h->stream));
+                CK(cudaMemcpyAsync(buf->as<double>(), B.tmp.as<double>(), 2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   h->stream));
+                h->launches += 1;
+            }
+            m = 2;
+            for (int j2 = 0; j2 < m; ++j2) {
+                st = subspace_column(h, B, n, ms, j2);
+                if (st != SPMPS_OK) return st;
+            }
+            reset = 1;
+            // coefficients of the current Ritz vector in the rotated basis: (scal[5], scal[6], 0, ...)
+            CK(cudaMemsetAsync(B.coef_prev.p, 0, 64 * sizeof(double), h->stream));
+            CK(cudaMemcpyAsync(B.coef_prev.p, sc + 5, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        } else {
+            CK(cudaMemsetAsync(B.coef_prev.p, 0, 64 * sizeof(double), h->stream));
+            CK(cudaMemcpyAsync(B.coef_prev.p, B.coef.p, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        }
+        // new direction into column m: t orthogonalised twice against V, normalised
+        double* tcol = V + static_cast<int64_t>(m) * n;
+        CK(cudaMemcpyAsync(tcol, tsrc, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        for (int pass = 0; pass < 2; ++pass) {
+            CK(launch_multidot(V, n, m, tcol, n, B.dot.as<double>(), h->partial.as<double>(), h->stream));
+            CK(launch_gemv(V, n, m, B.dot.as<double>(), n, tcol, 1, h->stream));
+            h->launches += 3;
+        }
+        CK(launch_norm2(tcol, n, sc + 3, h->partial.as<double>(), h->stream));
+        CK(launch_scale_inv_sqrt(tcol, n, sc + 3, h->stream));
+        h->launches += 3;
+        if (rec >= 0) prof_end(h, h->stream, rec);
+        // one host read per iteration: theta, kept metric directions, |r|^2, |t|^2
+        CK(cudaMemcpyAsync(host, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        int infer_err = 0;
+        if (learned) CK(cudaMemcpyAsync(&infer_err, ML.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         ++h->dav_iters;
+        if (infer_err) return fail(h, SPMPS_ERR_TIMEOUT, "learned correction: a bounded tensor-core wait gave up");
         if (host[1] < 0.5) return fail(h, SPMPS_ERR_SINGULAR_METRIC, "projected metric has no usable direction");
         if (!std::isfinite(host[0]) || !std::isfinite(host[2])) return fail(h, SPMPS_ERR_NAN, "non-finite Ritz value");
         const double theta = host[0], rn = std::sqrt(std::max(host[2], 0.0));
         out->theta = theta;
         out->resid = rn;
         out->iters = it;
-        if (rn < h->opt.dav_tol_r && std::fabs(theta - theta_prev) < h->opt.dav_tol_theta) {
+        if (rn < tol_r && std::fabs(theta - theta_prev) < tol_theta) {
             out->converged = true;
-            return SPMPS_OK;
+            return finish_harvest();
         }
         theta_prev = theta;
-        if (h->opt.precond == 1) {
-            st = metric_cg(h, k, B, n, B.r.as<double>(), B.t.as<double>());
-            if (st != SPMPS_OK) return st;
-        }
-        if (m == ms) {
-            // thick restart on [x, previous x]
-            CK(launch_restart_coef(B.coef.as<double>(), B.coef_prev.as<double>(), m, B.Q.as<double>(), sc + 4, h->stream));
-            double rq[3];
-            CK(cudaMemcpyAsync(rq, sc + 4, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-            CK(cudaStreamSynchronize(h->stream));
-            const int kr = static_cast<int>(rq[0] + 0.5);
-            for (DevMem* buf : {&B.V, &B.HV, &B.NV}) {
-                CK(launch_basis_rotate(buf->as<double>(), n, m, B.Q.as<double>(), m, kr, n, B.tmp.as<double>(), h->stream));
-                CK(cudaMemcpyAsync(buf->as<double>(), B.tmp.as<double>(), kr * n * sizeof(double), cudaMemcpyDeviceToDevice,
-                                   h->stream));
-                h->launches += 1;
-            }
-            m = kr;
-            for (int j = 0; j < m; ++j) {
-                st = subspace_column(h, B, n, ms, j);
+        if (!(host[3] > 1e-28)) {
+            // the correction lies in the basis: fall back to the diagonal correction (after a
+            // learned one), then to the residual itself
+            double nrm2 = 0.0;
+            if (learned) {
+                CK(cudaMemcpyAsync(tcol, B.t.as<double>(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+                st = orthogonalise(h, B, n, m, tcol, &nrm2);
                 if (st != SPMPS_OK) return st;
             }
-            // coefficients of the current Ritz vector in the rotated basis
-            double cp[64] = {0};
-            cp[0] = rq[1];
-            if (kr == 2) cp[1] = rq[2];
-            CK(cudaMemcpyAsync(B.coef_prev.p, cp, sizeof(cp), cudaMemcpyHostToDevice, h->stream));
-        } else {
-            CK(cudaMemsetAsync(B.coef_prev.p, 0, 64 * sizeof(double), h->stream));
-            CK(cudaMemcpyAsync(B.coef_prev.p, B.coef.p, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            if (!(nrm2 > 1e-28)) {
+                CK(cudaMemcpyAsync(tcol, B.r.as<double>(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+                st = orthogonalise(h, B, n, m, tcol, &nrm2);
+                if (st != SPMPS_OK) return st;
+            }
+            if (!(nrm2 > 1e-28)) return finish_harvest();  // the basis spans the reachable space
+            CK(launch_scale_inv_sqrt(tcol, n, sc + 3, h->stream));
+            ++h->launches;
         }
-        // new direction into column m
-        double* tcol = V + static_cast<int64_t>(m) * n;
-        CK(cudaMemcpyAsync(tcol, B.t.as<double>(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-        double nrm2 = 0.0;
-        st = orthogonalise(h, B, n, m, tcol, &nrm2);
-        if (st != SPMPS_OK) return st;
-        if (!(nrm2 > 1e-28)) {
-            CK(cudaMemcpyAsync(tcol, B.r.as<double>(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-            st = orthogonalise(h, B, n, m, tcol, &nrm2);
-            if (st != SPMPS_OK) return st;
-            if (!(nrm2 > 1e-28)) return SPMPS_OK;  // the basis spans the reachable space: stagnation
-        }
-        CK(launch_scale_inv_sqrt(tcol, n, B.scal.as<double>() + 3, h->stream));
-        ++h->launches;
         st = apply_column(h, k, B, n, m);
         if (st != SPMPS_OK) return st;
         st = subspace_column(h, B, n, ms, m);
         if (st != SPMPS_OK) return st;
         ++m;
     }
-    return SPMPS_OK;
+    return finish_harvest();
 }
 
 // ---- decimation ------------------------------------------------------------------------------
@@ -415,12 +527,14 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
     CK(B.sidx.ensure(std::max(3 * total, 1) * sizeof(int)));
     CK(B.sval.ensure(std::max(2 * total, 1) * sizeof(double)));
     CK(cudaMemsetAsync(B.status.p, 0, sizeof(int), h->stream));
+    const int rec_eig = h->profile ? prof_begin(h, h->stream, 4, 0.0) : -1;
     CK(launch_jacobi_batched(B.mats.as<double>(), B.vscr.as<double>(), B.evals.as<double>(), B.mat_off.as<int64_t>(),
                              B.val_off.as<int64_t>(), B.dims.as<int>(), nm, maxdim, h->opt.jacobi_smem_max,
                              B.status.as<int>(), h->stream));
     CK(launch_truncate(B.evals.as<double>(), B.val_off.as<int64_t>(), B.dims.as<int>(), B.ln.as<int>(), B.ltm.as<int>(),
                        nm, total, Dmax, kTieRtol, kDropAbs, B.keep.as<int>(), B.keep_total.as<int>(), B.disc.as<double>(),
                        B.sidx.as<int>(), B.sval.as<double>(), h->stream));
+    if (rec_eig >= 0) prof_end(h, h->stream, rec_eig);
     h->launches += 2;
     std::vector<int> keep(std::max(nm, 1));
     int jac_status = 0;

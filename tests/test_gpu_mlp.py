@@ -1,0 +1,105 @@
+"""Learned Davidson correction: device kernels against the CPU oracle (oracle/mlp.py).
+
+FP32 training kernels: loss and every gradient vs float64 NumPy on the same (FP32-rounded)
+parameters and batch.  Inference: the FP32 path vs float64, and the tensor-core path (BF16
+operands of the 256 x 256 layer, FP32 accumulation) vs the oracle forward with the same BF16
+rounding.  Then harvesting, training, and the learned correction inside Davidson.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as OM, mpo as M, mps as S
+from paper_1703_04789_gb300 import inputs
+from tests.gpu_util import require_gpu
+
+
+def _dev(L=6, N=6, D=16, G=4, **kw):
+    from paper_1703_04789_gb300 import Spmps
+    d = Spmps(L, N, 0, 0, G, D, **kw)
+    d.set_hubbard(1.0, 4.0)
+    return d
+
+
+def _params(seed):
+    p = OM.init_params(seed)
+    p["b1"] = np.random.default_rng(seed + 1).normal(0, 0.1, OM.HIDDEN)
+    p["b2"] = np.random.default_rng(seed + 2).normal(0, 0.1, OM.HIDDEN)
+    p["b3"] = np.array([0.05])
+    flat = OM.flatten(p).astype(np.float32)
+    return OM.unflatten(flat), flat
+
+
+@pytest.mark.gpu
+def test_training_gradients_match_oracle():
+    require_gpu()
+    dev = _dev()
+    p, flat = _params(1)
+    dev.mlp_set_params(flat)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((300, 4)).astype(np.float32)
+    T = rng.standard_normal(300).astype(np.float32)
+    loss, g = dev.mlp_loss_grad(X, T)
+    loss_ref, g_ref = OM.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - loss_ref) < 1e-5 * max(1.0, loss_ref)
+    gr = OM.flatten(g_ref)
+    scale = np.abs(gr).max()
+    assert np.abs(g - gr).max() < 2e-5 * scale, np.abs(g - gr).max() / scale
+    dev.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [1, 127, 1000, 4097])
+def test_inference_fp32_and_tensor_cores_match_oracle(n):
+    require_gpu()
+    dev = _dev()
+    p, flat = _params(3)
+    dev.mlp_set_params(flat)
+    rng = np.random.default_rng(n)
+    r = rng.standard_normal(n)
+    dh = rng.uniform(-2.0, 3.0, n)
+    dn = rng.uniform(0.0, 1.0, n)
+    theta = -0.7
+    X = OM.features(r, dh, dn, theta)
+    y_ref, _ = OM.forward(p, X)
+    t32 = dev.mlp_infer(r, dh, dn, theta, tensor_cores=False)
+    assert np.abs(t32 - y_ref).max() < 1e-4 * max(1.0, np.abs(y_ref).max())
+    # tensor-core path: the reference rounds the layer-2 operands to bf16; the features enter in
+    # float32, so that rounding is applied to them too before the comparison
+    y_bf = OM.forward_bf16_layer2(p, X.astype(np.float32).astype(np.float64))
+    ttc = dev.mlp_infer(r, dh, dn, theta, tensor_cores=True)
+    err = np.abs(ttc - y_bf).max() / max(1.0, np.abs(y_bf).max())
+    assert err < 2e-3, err
+    dev.close()
+
+
+@pytest.mark.gpu
+def test_harvest_train_and_learned_correction_in_davidson():
+    """Harvest pairs from plain (diagonal) sweeps, train, then run the same optimisation steps
+    from the same MPS with the learned correction: the converged theta must agree with the
+    diagonal solve; the iteration counts of both are reported."""
+    require_gpu()
+    L, N, D, G = 8, 8, 32, 5
+    labels, tens = inputs.random_mps(L, N, 0, D, 7)
+    dev = _dev(L, N, D, G, dav_tol_r=1e-7)
+    dev.set_mps(labels, tens, center=0)
+    dev.canonicalize()
+    dev.mlp_harvest(True, samples_per_iteration=256, capacity=1 << 20)
+    dev.sweep(2)
+    X, T = dev.mlp_data()
+    assert X.shape[0] > 1000 and np.isfinite(X).all() and np.isfinite(T).all()
+    dev.mlp_harvest(False)
+    l0, l1 = dev.mlp_train(400, batch=2048, lr=1e-3, seed=5)
+    assert l1 < l0, (l0, l1)
+    ckpt = dev.get_mps()
+    params = dev.mlp_get_params()
+    results = {}
+    for pre in ("diag", "learned"):
+        d2 = _dev(L, N, D, G, dav_tol_r=1e-7, precond=pre)
+        d2.mlp_set_params(params)
+        d2.set_mps(*ckpt[:2], center=ckpt[2])
+        th, it = d2.optimize_step(0, True, allow_not_converged=True)
+        results[pre] = (th, it)
+        d2.close()
+    print("learned correction: theta/iterations", results)
+    assert abs(results["learned"][0] - results["diag"][0]) < 1e-8 * max(1.0, abs(results["diag"][0]))
+    dev.close()
