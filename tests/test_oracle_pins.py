@@ -545,3 +545,55 @@ def test_bf16_rounding_matches_known_values():
     assert mlp.to_bf16(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6  # half-way, rounds to even (up)
     assert mlp.to_bf16(np.float32(1.0 + 2.0 ** -7)) == 1.0 + 2.0 ** -7      # representable
     assert mlp.to_bf16(np.float32(-3.0)) == -3.0
+
+
+# ---- spin-free properties (Eq. PropSpinFree) ------------------------------------------------
+
+def _prop_state(K, N, twoM, twoS, D, seed):
+    from oracle import properties as PR
+    h1, eri, _ = inputs.synthetic_active_space(K, seed)
+    labels, tens = inputs.random_mps(K, N, twoM, D, seed)
+    ng = Q.n_exact(K, N, twoM, twoS)
+    P = S.prepare(labels, tens, M.ab_initio_mpo(h1, eri), twoS, twoM, ng)
+    psi, ppsi, (Na, Nb, basis) = PR.projected_pair(P.mps, K, N, twoM, twoS, ng)
+    return P, h1, eri, psi, ppsi, Na, Nb
+
+
+@pytest.mark.parametrize("K,N,twoM,twoS", [(4, 4, 0, 0), (4, 5, 1, 3)])
+def test_fragment_energies_sum_to_the_energy(K, N, twoM, twoS):
+    """Eq. sumH grouped by spatial orbital: sum_p e_p is the projected energy, which the MPO
+    environment code computes independently."""
+    from oracle import properties as PR
+    P, h1, eri, psi, ppsi, Na, Nb = _prop_state(K, N, twoM, twoS, 8, 3)
+    e = [PR.expectation(PR.fragment_operator(K, Na, Nb, h1, eri, p), psi, ppsi) for p in range(K)]
+    E, _ = P.energy(0)
+    assert abs(sum(e) - E) < 1e-11
+
+
+def test_rdm1_trace_symmetry_and_spin_sum_rule():
+    """tr(gamma) = N, gamma symmetric with eigenvalues in [0, 2]; sum over all i, j of
+    <S_i . S_j> = S(S+1) for the projected state."""
+    from oracle import properties as PR
+    K, N, twoM, twoS = 4, 4, 0, 2
+    P, h1, eri, psi, ppsi, Na, Nb = _prop_state(K, N, twoM, twoS, 8, 4)
+    g = np.array([[PR.expectation(PR.excitation_operator(K, Na, Nb, p, q), psi, ppsi) for q in range(K)]
+                  for p in range(K)])
+    assert abs(np.trace(g) - N) < 1e-12
+    assert np.abs(g - g.T).max() < 1e-12
+    w = np.linalg.eigvalsh(g)
+    assert w.min() > -1e-12 and w.max() < 2.0 + 1e-12
+    s2 = PR.expectation(PR.spin_dot_operator(K, Na, Nb, range(K), range(K)), psi, ppsi)
+    assert abs(s2 - 0.5 * twoS * (0.5 * twoS + 1)) < 1e-11
+
+
+def test_seniority_closed_forms():
+    """The N_alpha = K sector has exactly K - N_beta = 2M singly occupied orbitals in every
+    determinant; a closed-shell determinant has none."""
+    from oracle import properties as PR
+    K, N, twoM = 5, 8, 2
+    P, h1, eri, psi, ppsi, Na, Nb = _prop_state(K, N, twoM, twoM, 6, 5)
+    assert abs(PR.expectation(PR.seniority_operator(K, Na, Nb), psi, ppsi) - twoM) < 1e-12
+    basis = fock.sector_basis(3, 1, 1)
+    v = np.zeros(len(basis))
+    v[int(np.nonzero(basis == np.uint64(0b11))[0][0])] = 1.0
+    assert abs(PR.expectation(PR.seniority_operator(3, 1, 1), v, v)) < 1e-15
