@@ -65,8 +65,12 @@ typedef struct {
     int precision;      /* bulk H_eff x block products: 0 = FP64 (default), 1 = TF32, 2 = 3xTF32
                            (tensor cores, FP32 accumulation).  N_eff x, environments, Davidson and
                            decimation stay FP64; with 1 or 2 each Davidson solve converges first
-                           with reduced-precision actions, then refines with FP64 actions from
-                           that vector to the FP64 tolerance. */
+                           with reduced-precision actions, then switches to FP64 actions in the
+                           same subspace and converges to the FP64 tolerance. */
+    int autotune;       /* 1: the first projected-action plan of each site times the candidate
+                           tile policies of the block GEMMs (phases A and C separately, CUDA
+                           events, a few actions on scratch vectors) and keeps the fastest for
+                           that site; 0 (default): the fixed least-padding policy. */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -91,11 +95,53 @@ const char* spmps_last_error(spmps_handle h);
 spmps_status spmps_set_hubbard(spmps_handle h, double t, double U);
 
 /* General Hamiltonian of Eq. sqH from one-electron integrals h1 (K*K, row-major) and
- * chemist two-electron integrals h2 = (pq|rs) (K^4 row-major, may be NULL) plus e_core.
- * The MPO builder for general h2 is not part of this build: with h2 != NULL the call
- * returns SPMPS_ERR_UNSUPPORTED unless h2 is zero except (pp|pp) (an on-site U), and h1 must
- * couple nearest neighbours only (|p-q| <= 1). */
+ * chemist two-electron integrals h2 = (pq|rs) (K^4 row-major, may be NULL) plus e_core
+ * (Eq. sumH: the paper's g_{pq,sr} = <pq|sr> = (ps|qr)).  Inputs are copied.  h1 must be
+ * symmetric and h2 Hermitian ((pq|rs) = (qp|sr)), else SPMPS_ERR_BAD_INPUT.  Integrals that
+ * couple only nearest neighbours (h1) and single orbitals ((pp|pp)) get the bond-dimension-6
+ * Hubbard-like MPO; all others the general MPO (Eq. sumH / Eq. Wfac): every term placed with
+ * complementary-operator channels, bond dimension 2 + 2 n_L + 2 n_R + O(min(n_L, n_R)^2) at a
+ * cut with n_L / n_R spin-orbitals on its sides.  The MPO site tensors live on the host (one
+ * copy per beta point); when they would need more than 4 GB the call returns
+ * SPMPS_ERR_UNSUPPORTED. */
 spmps_status spmps_set_hamiltonian(spmps_handle h, const double* h1, const double* h2, double ecore);
+
+/* Hamiltonian given directly as an MPO on spatial sites (an alternative to the integrals):
+ * bond_dims[0..K] (bond_dims[0] = bond_dims[K] = 1) and sites[k] = W[k] as a dense row-major
+ * (bond_dims[k], bond_dims[k+1], 4, 4) array, W[wl][wr][s][t] = <s| op |t> in the local basis
+ * {0, b, a, ab} (index 2 n_alpha + n_beta) with the Jordan-Wigner order of Eq. JWtrans.  The
+ * operator must conserve the particle number (checked: SPMPS_ERR_BAD_INPUT) and be Hermitian
+ * (not checked).  Inputs are copied. */
+spmps_status spmps_set_mpo(spmps_handle h, const int* bond_dims, const double* const* sites);
+
+/* Host-only (no device, no handle): the general MPO the library builds from integrals (same
+ * conventions as spmps_set_hamiltonian and spmps_set_mpo, without the Hermiticity check).
+ * First call with sites == NULL fills bond_dims[0..K]; the second copies W[k] into sites[k]
+ * (bond_dims[k] * bond_dims[k+1] * 16 doubles each). */
+spmps_status spmps_mpo_from_integrals(int K, const double* h1, const double* h2, double ecore, int* bond_dims,
+                                      double* const* sites);
+
+/* Initial MPS: the product state of a Slater determinant (Eq. FSMPS
+ * with all bond dimensions 1): occ[k] in {0 = empty, 1 = beta, 2 = alpha, 3 = both} for each
+ * spatial orbital k (the local index 2 n_alpha + n_beta).  The occupations must give the
+ * handle's (N, 2M), else SPMPS_ERR_BAD_INPUT.  Bond dimensions grow up to D in the two-site
+ * sweeps.  The centre is site 0. */
+spmps_status spmps_init_determinant(spmps_handle h, const int8_t* occ);
+
+/* Random initial MPS with the handle's (N, 2M) and bond dimension D: on every bond the labels
+ * (n, 2m) reachable from the left and completable on the right, dimensions in proportion to the
+ * smaller of the left and right Fock-sector sizes (largest-remainder rounding, total <= D),
+ * labels without a live neighbour removed; entries i.i.d. N(0, 1) from a SplitMix64 counter
+ * stream (Box-Muller) of `seed`; then canonicalised (spmps_canonicalize). */
+spmps_status spmps_init_random(spmps_handle h, uint64_t seed);
+
+/* Checkpoint file of the current MPS (labels, site tensors, centre, and the problem's K, N,
+ * 2M, 2S) in a little-endian binary format: 8-byte magic "SPMPSCK1", six int32 (K, N, 2M, 2S,
+ * centre, 0), the K+1 bond dimensions (int32), 2 int32 labels (n, 2m) per bond index, then the
+ * site tensors (D_k, 4, D_k+1) as float64.  spmps_load reads it into a handle with the same
+ * K, N and 2M (else SPMPS_ERR_BAD_INPUT) through spmps_set_mps. */
+spmps_status spmps_save(spmps_handle h, const char* path);
+spmps_status spmps_load(spmps_handle h, const char* path);
 
 /* Load an MPS.  bond_dims[i] (i = 0..K) is the dimension of bond i (bond_dims[0] =
  * bond_dims[K] = 1); labels holds 2*sum(bond_dims) ints: (n, 2m) per bond index, bond by bond,
@@ -187,6 +233,25 @@ spmps_status spmps_energy(spmps_handle h, double* E, double* norm_P);
 /* <S^2> of the projected state, through the same engine with the S^2 MPO of Eq. Sfac. */
 spmps_status spmps_expect_s2(spmps_handle h, double* s2);
 
+/* Spin-free properties (Eq. PropSpinFree): <O> = <Psi|O P|Psi> / <Psi|P|Psi> for an operator
+ * that commutes with the projector, through the same environments and projected action as the
+ * energy.  Each call builds the environments of O for every beta point (the handle's own
+ * environments are kept).  Errors as spmps_energy.
+ *
+ * spmps_expect_mpo: O given as an MPO in the spmps_set_mpo format (inputs copied).
+ * spmps_fragment_energies: e[p] (p = 0..K-1), the terms of Eq. sumH whose first creation operator
+ *   is on spatial orbital p, both spins: sum_p e[p] + e_core = E.  Needs the integrals of
+ *   spmps_set_hamiltonian or spmps_set_hubbard (SPMPS_ERR_STATE after spmps_set_mpo).
+ * spmps_rdm1: the spin-free one-particle density matrix gamma[p*K + q] = <E_pq>,
+ *   E_pq = sum_s a+_ps a_qs (K*K doubles; symmetric for the real wavefunctions of this library).
+ * spmps_spin_correlation: <S_X . S_Y> for orbital sets X (nx indices) and Y (ny indices).
+ * spmps_seniority: <Omega>, the number of singly occupied orbitals. */
+spmps_status spmps_expect_mpo(spmps_handle h, const int* bond_dims, const double* const* sites, double* value);
+spmps_status spmps_fragment_energies(spmps_handle h, double* e);
+spmps_status spmps_rdm1(spmps_handle h, double* gamma);
+spmps_status spmps_spin_correlation(spmps_handle h, const int* X, int nx, const int* Y, int ny, double* value);
+spmps_status spmps_seniority(spmps_handle h, double* value);
+
 /* Statistics: counts[0] = Davidson iterations of the last sweep, counts[1] = projected applies
  * issued, counts[2] = kernel launches issued by the library since the handle was created;
  * values[0] = algorithmic flops of one projected apply at the last site applied (symmetry-
@@ -194,6 +259,12 @@ spmps_status spmps_expect_s2(spmps_handle h, double* s2);
  * algorithmic flops of every projected apply issued since the handle was created.  Either
  * pointer may be NULL (counts holds 3, values 3). */
 spmps_status spmps_stats(spmps_handle h, int64_t* counts, double* values);
+
+/* Davidson iterations of the last spmps_sweep call: *iterations counts every iteration, and
+ * *refine_iterations the part spent in the FP64 refinement stage that follows a TF32 / 3xTF32
+ * stage (0 with precision 0).  Both are reset when spmps_sweep starts.  Either pointer may be
+ * NULL. */
+spmps_status spmps_davidson_stats(spmps_handle h, int64_t* iterations, int64_t* refine_iterations);
 
 /* Copy the current MPS to host memory (checkpoint).  First call with sites == NULL: fills
  * bond_dims[0..K] (and *center).  Second call: labels must hold 2 * sum(bond_dims) ints and sites[k]

@@ -38,7 +38,7 @@ class Options(C.Structure):
         ("batched", C.c_int), ("precond", C.c_int), ("cg_steps", C.c_int),
         ("dav_tol_r", C.c_double), ("dav_tol_theta", C.c_double),
         ("dav_max_sub", C.c_int), ("dav_max_iter", C.c_int), ("device", C.c_int),
-        ("jacobi_smem_max", C.c_int), ("precision", C.c_int),
+        ("jacobi_smem_max", C.c_int), ("precision", C.c_int), ("autotune", C.c_int),
     ]
 
 
@@ -65,6 +65,17 @@ def load_library(path: str | None = None):
         "spmps_last_error": (C.c_char_p, [H]),
         "spmps_set_hubbard": (i, [H, d, d]),
         "spmps_set_hamiltonian": (i, [H, P(d), P(d), d]),
+        "spmps_set_mpo": (i, [H, P(i), C.c_void_p]),
+        "spmps_init_determinant": (i, [H, P(C.c_int8)]),
+        "spmps_expect_mpo": (i, [H, P(i), C.c_void_p, P(d)]),
+        "spmps_fragment_energies": (i, [H, P(d)]),
+        "spmps_rdm1": (i, [H, P(d)]),
+        "spmps_spin_correlation": (i, [H, P(i), i, P(i), i, P(d)]),
+        "spmps_seniority": (i, [H, P(d)]),
+        "spmps_init_random": (i, [H, C.c_uint64]),
+        "spmps_save": (i, [H, C.c_char_p]),
+        "spmps_load": (i, [H, C.c_char_p]),
+        "spmps_mpo_from_integrals": (i, [i, P(d), P(d), d, P(i), C.c_void_p]),
         "spmps_set_mps": (i, [H, P(i), P(i), P(P(d)), i]),
         "spmps_x_layout": (i, [H, i, P(i64), P(i), P(i), P(i64), P(i), P(i)]),
         "spmps_apply_heff": (i, [H, i, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -80,6 +91,7 @@ def load_library(path: str | None = None):
         "spmps_energy": (i, [H, P(d), P(d)]),
         "spmps_expect_s2": (i, [H, P(d)]),
         "spmps_stats": (i, [H, P(i64), P(d)]),
+        "spmps_davidson_stats": (i, [H, P(i64), P(i64)]),
         "spmps_quadrature": (i, [H, P(d), P(d)]),
         "spmps_get_mps": (i, [H, P(i), P(i), C.c_void_p, P(i)]),
         "spmps_stream": (i, [H, P(C.c_void_p)]),
@@ -109,7 +121,7 @@ class Spmps:
 
     def __init__(self, K, N, twoM, twoS, n_beta, D, *, batched=True, precond="diag", cg_steps=5,
                  dav_tol_r=1e-6, dav_tol_theta=1e-10, dav_max_sub=20, dav_max_iter=200, device=0,
-                 jacobi_smem_max=0, precision="fp64"):
+                 jacobi_smem_max=0, precision="fp64", autotune=False):
         self.lib = load_library()
         o = Options()
         self.lib.spmps_default_options(C.byref(o))
@@ -119,6 +131,7 @@ class Spmps:
         o.dav_max_sub, o.dav_max_iter, o.device = dav_max_sub, dav_max_iter, device
         o.jacobi_smem_max = jacobi_smem_max
         o.precision = {"fp64": 0, "tf32": 1, "3xtf32": 2}[precision]
+        o.autotune = 1 if autotune else 0
         h = C.c_void_p()
         self._h = None
         self._check(self.lib.spmps_create(K, N, twoM, twoS, n_beta, D, C.byref(o), C.byref(h)), None)
@@ -154,6 +167,27 @@ class Spmps:
             h2 = np.ascontiguousarray(h2, dtype=np.float64)
             h2p = _dptr(h2)
         self._check(self.lib.spmps_set_hamiltonian(self._h, _dptr(h1), h2p, ecore))
+
+    def init_determinant(self, occ):
+        """Product-state MPS of a determinant: occ[k] in {0, 1 (beta), 2 (alpha), 3 (both)}."""
+        o = np.ascontiguousarray(occ, dtype=np.int8)
+        self._check(self.lib.spmps_init_determinant(self._h, o.ctypes.data_as(C.POINTER(C.c_int8))))
+
+    def init_random(self, seed: int):
+        self._check(self.lib.spmps_init_random(self._h, seed))
+
+    def save(self, path: str):
+        self._check(self.lib.spmps_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str):
+        self._check(self.lib.spmps_load(self._h, os.fsencode(path)))
+
+    def set_mpo(self, sites):
+        """Hamiltonian as an MPO: sites[k] of shape (Dl, Dr, 4, 4)."""
+        ws = [np.ascontiguousarray(w, dtype=np.float64) for w in sites]
+        dims = np.array([1] + [w.shape[1] for w in ws], dtype=np.int32)
+        arr = (C.POINTER(C.c_double) * self.K)(*[_dptr(w) for w in ws])
+        self._check(self.lib.spmps_set_mpo(self._h, dims.ctypes.data_as(C.POINTER(C.c_int)), C.cast(arr, C.c_void_p)))
 
     def set_mps(self, labels, tensors, center: int = 0):
         """labels: K+1 arrays (D_i, 2) of (n, 2m); tensors: K dense (D_i, 4, D_i+1) arrays."""
@@ -290,12 +324,52 @@ class Spmps:
         self._check(self.lib.spmps_expect_s2(self._h, C.byref(v)))
         return v.value
 
+    # ---- spin-free properties (Eq. PropSpinFree) ----------------------------------------------
+    def expect_mpo(self, sites):
+        ws = [np.ascontiguousarray(w, dtype=np.float64) for w in sites]
+        dims = np.array([1] + [w.shape[1] for w in ws], dtype=np.int32)
+        arr = (C.POINTER(C.c_double) * self.K)(*[_dptr(w) for w in ws])
+        v = C.c_double()
+        self._check(self.lib.spmps_expect_mpo(self._h, dims.ctypes.data_as(C.POINTER(C.c_int)), C.cast(arr, C.c_void_p),
+                                              C.byref(v)))
+        return v.value
+
+    def fragment_energies(self):
+        e = np.zeros(self.K)
+        self._check(self.lib.spmps_fragment_energies(self._h, _dptr(e)))
+        return e
+
+    def rdm1(self):
+        g = np.zeros((self.K, self.K))
+        self._check(self.lib.spmps_rdm1(self._h, _dptr(g)))
+        return g
+
+    def spin_correlation(self, X, Y):
+        x = np.ascontiguousarray(X, dtype=np.int32)
+        y = np.ascontiguousarray(Y, dtype=np.int32)
+        v = C.c_double()
+        self._check(self.lib.spmps_spin_correlation(self._h, x.ctypes.data_as(C.POINTER(C.c_int)), len(x),
+                                                    y.ctypes.data_as(C.POINTER(C.c_int)), len(y), C.byref(v)))
+        return v.value
+
+    def seniority(self):
+        v = C.c_double()
+        self._check(self.lib.spmps_seniority(self._h, C.byref(v)))
+        return v.value
+
     def stats(self):
         c = (C.c_int64 * 3)()
         v = (C.c_double * 3)()
         self._check(self.lib.spmps_stats(self._h, c, v))
         return {"davidson_iterations": c[0], "applies": c[1], "launches": c[2],
                 "apply_flops": v[0], "discarded_weight": v[1], "apply_flops_total": v[2]}
+
+    def davidson_stats(self):
+        """(iterations, FP64 refinement iterations) of the last sweep."""
+        a = C.c_int64()
+        b = C.c_int64()
+        self._check(self.lib.spmps_davidson_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def get_mps(self):
         """Checkpoint: (labels, tensors, center) in the format set_mps reads."""
@@ -383,6 +457,30 @@ class Spmps:
         c = np.zeros(self.n_beta)
         self._check(self.lib.spmps_quadrature(self._h, _dptr(b), _dptr(c)))
         return b, c
+
+
+def mpo_from_integrals(h1, h2=None, ecore: float = 0.0):
+    """The library's general MPO for integrals h1 (K x K) and chemist h2 (K^4): a list of
+    (Dl, Dr, 4, 4) site tensors.  Host only."""
+    lib = load_library()
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    K = h1.shape[0]
+    h2p = None
+    if h2 is not None:
+        h2 = np.ascontiguousarray(h2, dtype=np.float64)
+        h2p = h2.ctypes.data_as(C.POINTER(C.c_double))
+    dims = np.zeros(K + 1, dtype=np.int32)
+    st = lib.spmps_mpo_from_integrals(K, h1.ctypes.data_as(C.POINTER(C.c_double)), h2p, ecore,
+                                      dims.ctypes.data_as(C.POINTER(C.c_int)), None)
+    if st != 0:
+        raise SpmpsError(st, lib.spmps_last_error(None).decode())
+    ws = [np.zeros((int(dims[k]), int(dims[k + 1]), 4, 4)) for k in range(K)]
+    arr = (C.POINTER(C.c_double) * K)(*[_dptr(w) for w in ws])
+    st = lib.spmps_mpo_from_integrals(K, h1.ctypes.data_as(C.POINTER(C.c_double)), h2p, ecore,
+                                      dims.ctypes.data_as(C.POINTER(C.c_int)), C.cast(arr, C.c_void_p))
+    if st != 0:
+        raise SpmpsError(st, lib.spmps_last_error(None).decode())
+    return ws
 
 
 def device_fp64_peak(device: int = 0) -> float:

@@ -57,19 +57,32 @@ struct ColLayout {
 ColLayout make_col_layout(const Bond& right, int n0, int ns, int sign);
 
 // ---------------------------------------------------------------------------------------------
-// MPO: W[k][((wl*dwr + wr)*4 + s)*4 + t], s = output (bra) index, t = input (ket) index.
+// MPO site tensors, stored sparsely: per site k the entries (wl, wr, op) with op[s*4 + t] =
+// <s| W[k][wl][wr] |t> (s = output/bra index, t = input/ket index).  Built by add() (entries with
+// the same (wl, wr) accumulate), then finalize(): entries sorted by (wr, wl), all-zero ones
+// dropped, and the per-wr / per-wl indices filled.
+struct MpoEntry {
+    int wl, wr;
+    double op[16];
+};
 struct MPO {
     int K = 0;
-    std::vector<int> dw;                 // K+1 bond dimensions, dw[0] = dw[K] = 1
-    std::vector<std::vector<int>> cn;    // per bond, per channel: particle-number charge
-    std::vector<std::vector<double>> W;  // per site
-    double& at(int k, int wl, int wr, int s, int t) {
-        return W[k][((static_cast<size_t>(wl) * dw[k + 1] + wr) * 4 + s) * 4 + t];
-    }
-    double get(int k, int wl, int wr, int s, int t) const {
-        return W[k][((static_cast<size_t>(wl) * dw[k + 1] + wr) * 4 + s) * 4 + t];
-    }
+    std::vector<int> dw;                  // K+1 bond dimensions, dw[0] = dw[K] = 1
+    std::vector<std::vector<int>> cn;     // per bond, per channel: particle-number charge
+    std::vector<std::vector<MpoEntry>> E; // per site
+    std::vector<std::vector<int>> wr_ptr; // per site: entries with wr = u are E[k][wr_ptr[u] .. wr_ptr[u+1])
+    std::vector<std::vector<int>> by_wl;  // per site: entry indices ordered by (wl, wr)
+    std::vector<std::vector<int>> wl_ptr; // per site: by_wl[k][wl_ptr[w] .. wl_ptr[w+1]) have wl = w
+
+    void init(int K_, const std::vector<int>& dims);
+    void add(int k, int wl, int wr, const double* op, double scale = 1.0);
+    void finalize();
+    double get(int k, int wl, int wr, int s, int t) const;  // lookup by binary search
+    size_t entries() const;
     bool finalize_charges(std::string* err);  // derive cn from the nonzero pattern
+
+  private:
+    std::vector<std::vector<std::pair<uint64_t, int>>> pending_;  // unsorted (key, entry) while building
 };
 MPO mpo_hubbard(int K, double t, double U);
 // General nearest-neighbour one-band Hamiltonian: on-site energies eps (K), hoppings hop (K-1)
@@ -77,6 +90,10 @@ MPO mpo_hubbard(int K, double t, double U);
 MPO mpo_nearest_neighbour(int K, const std::vector<double>& eps, const std::vector<double>& hop,
                           const std::vector<double>& U, double ecore);
 MPO mpo_s2(int K);
+// General second-quantised Hamiltonian of Eq. sqH from spatial integrals h1 (K x K) and chemist
+// (pq|rs) (K^4, may be NULL), built term by term with complementary-operator channels; false and
+// a message when the result would not fit (bond dimension above max_dw).
+bool mpo_ab_initio(int K, const double* h1, const double* h2, double ecore, int max_dw, MPO* out, std::string* err);
 MPO mpo_identity(int K);
 MPO mpo_rotated(const MPO& m, double beta);  // W . r(beta) on the ket leg (Eq. expSy)
 
@@ -147,13 +164,24 @@ struct DiagTerm {
 };
 
 // A host-side plan of grouped GEMMs.
+// Tile policy of a grouped GEMM: tasks with a total reduction length >= wb_kmin and at most
+// wb_mn_max outputs get warp-block tiles (shape 5) of about wb_elems outputs per warp; the rest
+// the register-tiled shape with the least padding.
+struct TilePolicy {
+    int wb_kmin = 64;
+    int wb_mn_max = 4096;
+    int wb_elems = 256;
+};
+constexpr int kTileCandidates = 6;
+TilePolicy tile_candidate(int i);  // i = 0 is the default policy
+
 struct GemmPlan {
     std::vector<GemmTask> tasks;
     std::vector<GemmSeg> segs;
     std::vector<GemmTile> tiles;
     std::vector<int> cmaps;
     double flops = 0.0;
-    void add_tiles();  // tiles of the shape with the least padding per task
+    void add_tiles(const TilePolicy& pol = TilePolicy());
     void clear() { tasks.clear(); segs.clear(); tiles.clear(); cmaps.clear(); flops = 0.0; }
 };
 struct CombPlan {

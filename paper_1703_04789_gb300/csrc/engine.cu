@@ -14,7 +14,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
+#include <unordered_map>
 
 #include "engine.h"
 
@@ -113,6 +115,8 @@ bool in_range(uint64_t hd, int64_t last, const int64_t* sizes, std::string* why,
     return true;
 }
 
+bool validate_tiles(const GemmPlan& G, std::string* why);
+
 bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why) {
     for (const GemmTask& T : G.tasks) {
         if (T.M <= 0 || T.N <= 0) { *why = "empty GEMM task"; return false; }
@@ -138,6 +142,10 @@ bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why) {
                 return false;
         }
     }
+    return validate_tiles(G, why);
+}
+
+bool validate_tiles(const GemmPlan& G, std::string* why) {
     for (const GemmTile& t : G.tiles) {
         if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 5) {
             *why = "bad tile";
@@ -187,8 +195,12 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
             h->prof_ms[5] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
     } done{h, t0};
-    P.A.add_tiles();
-    P.C.add_tiles();
+    P.A.add_tiles(P.polA);
+    P.C.add_tiles(P.polC);
+    {
+        std::string why;
+        if (!validate_tiles(P.A, &why) || !validate_tiles(P.C, &why)) return fail(h, SPMPS_ERR_CUDA, "internal tile check: " + why);
+    }
     CK(upload(P.d_tasksA, P.A.tasks, h->stream));
     CK(upload(P.d_segsA, P.A.segs, h->stream));
     CK(upload(P.d_tilesA, P.A.tiles, h->stream));
@@ -407,12 +419,14 @@ void build_left_plan(spmps_t* h, int i, const EnvStore& Lo, const EnvStore& Ln, 
                         O.cols = br.groups[CL.group[s]].dim;
                         O.ld = CL.width;
                         O.term0 = static_cast<int>(P.B.terms.size());
-                        for (int w = 0; w < dwl; ++w) {
+                        for (int ei = W.wr_ptr[i][u]; ei < W.wr_ptr[i][u + 1]; ++ei) {
+                            const MpoEntry& e = W.E[i][ei];
+                            const int w = e.wl;
                             const int64_t s1 = o1[w * ngl + ga];
                             if (s1 < 0) continue;
                             const ColLayout& C1 = c1[w * ngl + ga];
                             for (int t = 0; t < 4; ++t) {
-                                const double cf = W.get(i, w, u, s, t);
+                                const double cf = e.op[s * 4 + t];
                                 if (cf == 0.0 || C1.col[t] < 0) continue;
                                 CombTerm tm{};
                                 tm.src = handle(3, s1 + C1.col[t]);
@@ -562,12 +576,14 @@ void build_right_plan(spmps_t* h, int i, const EnvStore& Ro, const EnvStore& Rn,
                         O.cols = bl.groups[CL.group[s]].dim;
                         O.ld = CL.width;
                         O.term0 = static_cast<int>(P.B.terms.size());
-                        for (int u = 0; u < dwr; ++u) {
+                        for (int q = W.wl_ptr[i][w]; q < W.wl_ptr[i][w + 1]; ++q) {
+                            const MpoEntry& e = W.E[i][W.by_wl[i][q]];
+                            const int u = e.wr;
                             const int64_t s1 = o1[u * ngr + gb];
                             if (s1 < 0) continue;
                             const ColLayout& C1 = c1[u * ngr + gb];
                             for (int t = 0; t < 4; ++t) {
-                                const double cf = W.get(i, w, u, s, t);
+                                const double cf = e.op[s * 4 + t];
                                 if (cf == 0.0 || C1.col[t] < 0) continue;
                                 CombTerm tm{};
                                 tm.src = handle(3, s1 + C1.col[t]);
@@ -632,6 +648,12 @@ void build_right_plan(spmps_t* h, int i, const EnvStore& Ro, const EnvStore& Rn,
     P.flops = P.A.flops + P.B.flops + P.C.flops;
 }
 
+// diagonal WW coefficients of one channel pair (w, u), per two-site local state
+struct DiagPair {
+    int w, u;
+    double c[16];
+};
+
 // ---- the projected action plan ---------------------------------------------------------------
 // Slots: 0 = x, 1 = y, 2 = z, 3 = T1, 4 = T3, 5 = L(bond k), 6 = R(bond k+2).
 void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re, Plan& P) {
@@ -663,10 +685,11 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
     int64_t t1 = 0, t3 = 0;
     // per (op, g): offsets of T3 blocks for the output phase, kept for all g
     std::vector<std::vector<int64_t>> o3_all(static_cast<size_t>(nops) * G);
+    std::vector<std::vector<DiagPair>> diag_all(static_cast<size_t>(nops) * G);
     std::vector<std::vector<ColLayout>> c3_all(static_cast<size_t>(nops) * G);
     for (int op = 0; op < nops; ++op) {
         const MPO& m = h->ops.mpo[op];
-        const int dwl = m.dw[k], dwm = m.dw[k + 1], dwr = m.dw[k + 2];
+        const int dwl = m.dw[k], dwr = m.dw[k + 2];
         const std::vector<int>& cnl = m.cn[k];
         const std::vector<int>& cnr = m.cn[k + 2];
         for (int g = 0; g < G; ++g) {
@@ -676,23 +699,65 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
             P.tileA_rng[og] = static_cast<int>(P.A.tasks.size());
             P.combB_rng[og] = static_cast<int>(P.B.outs.size());
             const double fa0 = P.A.flops, fb0 = P.B.flops;
-            // WW[w][u][s][t] = c_g sum_v W_k[w,v,s1,t1] W_k+1[v,u,s2,t2]
-            std::vector<double> WW(static_cast<size_t>(dwl) * dwr * 256, 0.0);
-            for (int w = 0; w < dwl; ++w)
-                for (int v = 0; v < dwm; ++v)
+            // WW[w][u][(s1 s2)][(t1 t2)] = c_g sum_v W_k[w,v,s1,t1] W_k+1[v,u,s2,t2], kept for the
+            // (w, u) pairs joined by some v; ww_u[u] lists (w, pair) ordered by w
+            std::unordered_map<uint64_t, int> ww_id;
+            std::vector<std::array<double, 256>> ww;
+            std::vector<std::vector<std::pair<int, int>>> ww_u(dwr);
+            for (const MpoEntry& a : W.E[k]) {
+                const int v = a.wr;
+                for (int q = W.wl_ptr[k + 1][v]; q < W.wl_ptr[k + 1][v + 1]; ++q) {
+                    const MpoEntry& b = W.E[k + 1][W.by_wl[k + 1][q]];
+                    const uint64_t key = (static_cast<uint64_t>(a.wl) << 32) | static_cast<uint32_t>(b.wr);
+                    auto it = ww_id.find(key);
+                    int id;
+                    if (it == ww_id.end()) {
+                        id = static_cast<int>(ww.size());
+                        ww_id.emplace(key, id);
+                        ww.emplace_back();
+                        ww.back().fill(0.0);
+                        ww_u[b.wr].push_back({a.wl, id});
+                    } else {
+                        id = it->second;
+                    }
+                    std::array<double, 256>& dst = ww[id];
                     for (int s1 = 0; s1 < 4; ++s1)
                         for (int t1i = 0; t1i < 4; ++t1i) {
-                            const double a = W.get(k, w, v, s1, t1i);
-                            if (a == 0.0) continue;
-                            for (int u = 0; u < dwr; ++u)
-                                for (int s2 = 0; s2 < 4; ++s2)
-                                    for (int t2i = 0; t2i < 4; ++t2i) {
-                                        const double b = W.get(k + 1, v, u, s2, t2i);
-                                        if (b == 0.0) continue;
-                                        WW[((static_cast<size_t>(w) * dwr + u) * 16 + (s1 * 4 + s2)) * 16 + (t1i * 4 + t2i)] +=
-                                            cgw * a * b;
-                                    }
+                            const double av = a.op[s1 * 4 + t1i];
+                            if (av == 0.0) continue;
+                            for (int s2 = 0; s2 < 4; ++s2)
+                                for (int t2i = 0; t2i < 4; ++t2i) {
+                                    const double bv = b.op[s2 * 4 + t2i];
+                                    if (bv == 0.0) continue;
+                                    dst[(s1 * 4 + s2) * 16 + (t1i * 4 + t2i)] += cgw * av * bv;
+                                }
                         }
+                }
+            }
+            for (auto& lst : ww_u) std::sort(lst.begin(), lst.end());
+            // diagonal coefficients of the pairs between charge-0 channels, for the preconditioner
+            {
+                std::vector<DiagPair>& dp = diag_all[og];
+                dp.clear();
+                for (int u = 0; u < dwr; ++u) {
+                    if (cnr[u] != 0) continue;
+                    for (const auto& wp : ww_u[u]) {
+                        if (cnl[wp.first] != 0) continue;
+                        DiagPair d{};
+                        d.w = wp.first;
+                        d.u = u;
+                        bool any = false;
+                        for (int q = 0; q < 16; ++q) {
+                            d.c[q] = ww[wp.second][q * 16 + q];
+                            any = any || d.c[q] != 0.0;
+                        }
+                        if (any) dp.push_back(d);
+                    }
+                }
+                std::sort(dp.begin(), dp.end(), [](const DiagPair& a, const DiagPair& b) {
+                    return a.w != b.w ? a.w < b.w : a.u < b.u;
+                });
+            }
             // phase A
             std::vector<int64_t> o1(static_cast<size_t>(dwl) * ngl, -1);
             std::vector<ColLayout> c1(static_cast<size_t>(dwl) * ngl);
@@ -752,12 +817,14 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                         O.cols = br.groups[CL.group[s]].dim;
                         O.ld = CL.width;
                         O.term0 = static_cast<int>(P.B.terms.size());
-                        for (int w = 0; w < dwl; ++w) {
+                        for (const auto& wp : ww_u[u]) {
+                            const int w = wp.first;
                             const int64_t s1 = o1[w * ngl + ga];
                             if (s1 < 0) continue;
                             const ColLayout& C1 = c1[w * ngl + ga];
+                            const std::array<double, 256>& cw = ww[wp.second];
                             for (int t = 0; t < 16; ++t) {
-                                const double cf = WW[((static_cast<size_t>(w) * dwr + u) * 16 + s) * 16 + t];
+                                const double cf = cw[s * 16 + t];
                                 if (cf == 0.0 || C1.col[t] < 0) continue;
                                 CombTerm tm{};
                                 tm.src = handle(3, s1 + C1.col[t]);
@@ -774,8 +841,6 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                     c3[u * ngl + ga] = CL;
                 }
             P.flops_op[op] += (P.A.flops - fa0) + (P.B.flops - fb0);
-            // diagonal terms: WWdiag[w,u,s] with cn[w] = cn[u] = 0 (diagonal environment blocks)
-            (void)dwm;
         }
     }
     // phase C: one task per (N, M)-allowed output block and beta point, writing the partial sum
@@ -838,10 +903,9 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
     P.t2_size = t3;
     P.flops = P.A.flops + P.B.flops + P.C.flops;
 
-    // diagonal of the projected operators on the x layout
+    // diagonal of the projected operators on the x layout: for each output block and beta point,
+    // the pairs (w, u) of charge-0 channels with a nonzero diagonal WW coefficient
     for (int op = 0; op < nops; ++op) {
-        const MPO& m = h->ops.mpo[op];
-        const int dwl = m.dw[k], dwm = m.dw[k + 1], dwr = m.dw[k + 2];
         for (size_t la = 0; la < bl.labels.size(); ++la) {
             const Label& La = bl.labels[la];
             const int ga = La.group;
@@ -857,31 +921,23 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                 B.ld = xl.width[la];
                 B.out = op;
                 B.term0 = static_cast<int>(P.diag_terms.size());
-                const int s1 = s >> 2, s2 = s & 3;
                 for (int g = 0; g < G; ++g) {
-                    const MPO& W = h->ops.rot[op][g];
                     const int og = op * G + g;
-                    for (int w = 0; w < dwl; ++w) {
-                        if (m.cn[k][w] != 0) continue;
-                        const int64_t loff = Le.lay[op].off[w * ngl + ga];
+                    for (const DiagPair& d : diag_all[og]) {
+                        const double cf = d.c[s];
+                        if (cf == 0.0) continue;
+                        const int64_t loff = Le.lay[op].off[d.w * ngl + ga];
                         if (loff < 0) continue;
-                        for (int u = 0; u < dwr; ++u) {
-                            if (m.cn[k + 2][u] != 0) continue;
-                            const int64_t roff = Re.lay[op].off[u * ngr + gb];
-                            if (roff < 0) continue;
-                            double cf = 0.0;
-                            for (int v = 0; v < dwm; ++v) cf += W.get(k, w, v, s1, s1) * W.get(k + 1, v, u, s2, s2);
-                            cf *= h->cg[g];
-                            if (cf == 0.0) continue;
-                            const int gdl = bl.groups[ga].dim, gdr = br.groups[gb].dim;
-                            DiagTerm t{};
-                            t.l = handle(5, Le.base[og] + loff + static_cast<int64_t>(La.off - bl.groups[ga].off) * (gdl + 1));
-                            t.l_step = gdl + 1;
-                            t.r = handle(6, Re.base[og] + roff + static_cast<int64_t>(Lb.off - br.groups[gb].off) * (gdr + 1));
-                            t.r_step = gdr + 1;
-                            t.coef = cf;
-                            P.diag_terms.push_back(t);
-                        }
+                        const int64_t roff = Re.lay[op].off[d.u * ngr + gb];
+                        if (roff < 0) continue;
+                        const int gdl = bl.groups[ga].dim, gdr = br.groups[gb].dim;
+                        DiagTerm t{};
+                        t.l = handle(5, Le.base[og] + loff + static_cast<int64_t>(La.off - bl.groups[ga].off) * (gdl + 1));
+                        t.l_step = gdl + 1;
+                        t.r = handle(6, Re.base[og] + roff + static_cast<int64_t>(Lb.off - br.groups[gb].off) * (gdr + 1));
+                        t.r_step = gdr + 1;
+                        t.coef = cf;
+                        P.diag_terms.push_back(t);
                     }
                 }
                 B.nterm = static_cast<int>(P.diag_terms.size()) - B.term0;
@@ -990,6 +1046,63 @@ void invalidate_all(spmps_t* h) {
     for (auto& p : h->apply_plans) p.reset();
 }
 
+// Autotuner: time every tile candidate for phases A and C of the site's action plan (one warm-up
+// and two timed actions each on zero scratch vectors, CUDA events around the phases) and keep
+// the fastest per phase; the choice is cached per site for the life of the handle.
+spmps_status tune_apply_plan(spmps_t* h, int k, Plan& P) {
+    if (h->tune_a.size() != static_cast<size_t>(h->K)) {
+        h->tune_a.assign(h->K, -1);
+        h->tune_c.assign(h->K, -1);
+    }
+    if (h->tune_a[k] < 0) {
+        const int64_t nx = std::max<int64_t>(1, P.reduce_nx);
+        CK(h->tunebuf.ensure(3 * nx * sizeof(double)));
+        CK(cudaMemsetAsync(h->tunebuf.p, 0, 3 * nx * sizeof(double), h->stream));
+        CK(h->work3.ensure(std::max<int64_t>(1, 2 * static_cast<int64_t>(h->G) * P.reduce_nx) * sizeof(double)));
+        cudaEvent_t ev[5];
+        for (auto& e : ev) CK(cudaEventCreate(&e));
+        float best_a = INFINITY, best_c = INFINITY;
+        int ia = 0, ic = 0;
+        spmps_status st = SPMPS_OK;
+        for (int c = 0; c < kTileCandidates && st == SPMPS_OK; ++c) {
+            P.polA = P.polC = tile_candidate(c);
+            st = plan_upload(h, P);
+            if (st != SPMPS_OK) break;
+            Slots S{};
+            S.p[0] = h->tunebuf.as<double>();
+            S.p[1] = S.p[0] + nx;
+            S.p[2] = S.p[0] + 2 * nx;
+            S.p[3] = h->work1.as<double>();
+            S.p[4] = h->work2.as<double>();
+            S.p[5] = h->Lenv[k].buf.as<double>();
+            S.p[6] = h->Renv[k + 2].buf.as<double>();
+            S.p[8] = h->work3.as<double>();
+            S.p[9] = h->work3.as<double>() + static_cast<int64_t>(h->G) * P.reduce_nx;
+            float ta = 0.0f, tc = 0.0f;
+            for (int rep = 0; rep < 3 && st == SPMPS_OK; ++rep) {
+                st = plan_run(h, P, S, 0, 2 * h->G, h->stream, ev);
+                if (st != SPMPS_OK) break;
+                if (cudaEventSynchronize(ev[4]) != cudaSuccess) { st = fail(h, SPMPS_ERR_CUDA, "autotune timing"); break; }
+                if (rep == 0) continue;
+                float a = 0.0f, cc = 0.0f;
+                cudaEventElapsedTime(&a, ev[1], ev[2]);
+                cudaEventElapsedTime(&cc, ev[3], ev[4]);
+                ta += a;
+                tc += cc;
+            }
+            if (ta < best_a) { best_a = ta; ia = c; }
+            if (tc < best_c) { best_c = tc; ic = c; }
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        if (st != SPMPS_OK) return st;
+        h->tune_a[k] = ia;
+        h->tune_c[k] = ic;
+    }
+    P.polA = tile_candidate(h->tune_a[k]);
+    P.polC = tile_candidate(h->tune_c[k]);
+    return SPMPS_OK;
+}
+
 spmps_status get_apply_plan(spmps_t* h, int k, Plan** out) {
     spmps_status st = ensure_envs(h, k);
     if (st != SPMPS_OK) return st;
@@ -1008,6 +1121,10 @@ spmps_status get_apply_plan(spmps_t* h, int k, Plan** out) {
             sz[8] = sz[9] = static_cast<int64_t>(h->G) * nx;
             std::string why;
             if (!validate_plan(*P, sz, &why)) return fail(h, SPMPS_ERR_CUDA, "internal plan check (apply): " + why);
+        }
+        if (h->opt.autotune) {
+            st = tune_apply_plan(h, k, *P);
+            if (st != SPMPS_OK) return st;
         }
         st = plan_upload(h, *P);
         if (st != SPMPS_OK) return st;
@@ -1138,6 +1255,7 @@ void spmps_default_options(spmps_options* o) {
     o->device = 0;
     o->jacobi_smem_max = 0;
     o->precision = 0;
+    o->autotune = 0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1162,6 +1280,7 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (o.jacobi_smem_max == 0) o.jacobi_smem_max = 112;
     if (o.precond < 0 || o.precond > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precond must be 0, 1 or 2");
     if (o.precision < 0 || o.precision > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precision must be 0, 1 or 2");
+    if (o.autotune != 0 && o.autotune != 1) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "autotune must be 0 or 1");
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
     if (ce != cudaSuccess || ndev <= o.device)
@@ -1212,41 +1331,160 @@ spmps_status spmps_destroy(spmps_handle h) {
 spmps_status spmps_set_hubbard(spmps_handle h, double t, double U) {
     if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
     if (!std::isfinite(t) || !std::isfinite(U)) return fail(h, SPMPS_ERR_BAD_INPUT, "t and U must be finite");
-    return set_ops(h, mpo_hubbard(h->K, t, U));
+    const int K = h->K;
+    const size_t Kz = static_cast<size_t>(K);
+    std::vector<double> h1(Kz * Kz, 0.0), h2(Kz * Kz * Kz * Kz, 0.0);
+    for (int p = 0; p + 1 < K; ++p) h1[p * K + p + 1] = h1[(p + 1) * K + p] = -t;
+    for (size_t p = 0; p < Kz; ++p) h2[((p * Kz + p) * Kz + p) * Kz + p] = U;
+    spmps_status st = set_ops(h, mpo_hubbard(K, t, U));
+    if (st != SPMPS_OK) return st;
+    h->ints_h1.swap(h1);
+    h->ints_h2.swap(h2);
+    h->ints_ecore = 0.0;
+    return SPMPS_OK;
 }
+
+namespace {
+// Integrals that only couple nearest neighbours (h1) and repeat one orbital ((pp|pp)) take the
+// bond-dimension-6 Hubbard-like MPO; anything else the general builder.
+bool nearest_neighbour_only(int K, const double* h1, const double* h2) {
+    for (int p = 0; p < K; ++p)
+        for (int q = 0; q < K; ++q)
+            if (std::abs(p - q) > 1 && h1[p * K + q] != 0.0) return false;
+    if (!h2) return true;
+    const size_t Kz = static_cast<size_t>(K);
+    for (size_t p = 0; p < Kz; ++p)
+        for (size_t q = 0; q < Kz; ++q)
+            for (size_t r = 0; r < Kz; ++r)
+                for (size_t s = 0; s < Kz; ++s)
+                    if (h2[((p * Kz + q) * Kz + r) * Kz + s] != 0.0 && !(p == q && q == r && r == s)) return false;
+    return true;
+}
+
+spmps_status check_integrals(spmps_t* h, int K, const double* h1, const double* h2, double ecore) {
+    if (!h1) return fail(h, SPMPS_ERR_BAD_INPUT, "h1 is NULL");
+    if (!std::isfinite(ecore)) return fail(h, SPMPS_ERR_BAD_INPUT, "ecore not finite");
+    for (int p = 0; p < K * K; ++p)
+        if (!std::isfinite(h1[p])) return fail(h, SPMPS_ERR_BAD_INPUT, "h1 not finite");
+    if (h2) {
+        const size_t n4 = static_cast<size_t>(K) * K * K * K;
+        for (size_t i = 0; i < n4; ++i)
+            if (!std::isfinite(h2[i])) return fail(h, SPMPS_ERR_BAD_INPUT, "h2 not finite");
+    }
+    return SPMPS_OK;
+}
+
+// the library's MPO site tensors (one copy per beta point) are held on the host: keep them within this size
+constexpr double kMaxMpoHostBytes = 4.0e9;
+
+bool mpo_fits(const MPO& m, int copies, std::string* why) {
+    const double bytes = static_cast<double>(m.entries()) * sizeof(MpoEntry);
+    if (bytes * copies > kMaxMpoHostBytes) {
+        if (why) *why = "MPO site tensors need " + std::to_string(bytes * copies / 1e9) + " GB of host memory";
+        return false;
+    }
+    return true;
+}
+}  // namespace
 
 spmps_status spmps_set_hamiltonian(spmps_handle h, const double* h1, const double* h2, double ecore) {
     if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
-    if (!h1) return fail(h, SPMPS_ERR_BAD_INPUT, "h1 is NULL");
-    if (!std::isfinite(ecore)) return fail(h, SPMPS_ERR_BAD_INPUT, "ecore not finite");
     const int K = h->K;
-    std::vector<double> eps(K), hop(K > 1 ? K - 1 : 0), U(K, 0.0);
+    spmps_status st = check_integrals(h, K, h1, h2, ecore);
+    if (st != SPMPS_OK) return st;
+    // Davidson needs a Hermitian H: h_pq = h_qp and (pq|rs) = (qp|sr) for real orbitals
     for (int p = 0; p < K; ++p)
-        for (int q = 0; q < K; ++q) {
-            const double v = h1[p * K + q];
-            if (!std::isfinite(v)) return fail(h, SPMPS_ERR_BAD_INPUT, "h1 not finite");
-            if (std::fabs(v - h1[q * K + p]) > 1e-14 * (1.0 + std::fabs(v)))
+        for (int q = 0; q < p; ++q)
+            if (std::fabs(h1[p * K + q] - h1[q * K + p]) > 1e-12 * (1.0 + std::fabs(h1[p * K + q])))
                 return fail(h, SPMPS_ERR_BAD_INPUT, "h1 is not symmetric");
-            if (std::abs(p - q) > 1 && v != 0.0)
-                return fail(h, SPMPS_ERR_UNSUPPORTED, "h1 beyond nearest neighbours needs the general MPO builder");
-        }
-    for (int p = 0; p < K; ++p) eps[p] = h1[p * K + p];
-    for (int p = 0; p + 1 < K; ++p) hop[p] = h1[p * K + p + 1];
     if (h2) {
         const size_t Kz = static_cast<size_t>(K);
         for (size_t p = 0; p < Kz; ++p)
             for (size_t q = 0; q < Kz; ++q)
                 for (size_t r = 0; r < Kz; ++r)
-                    for (size_t s = 0; s < Kz; ++s) {
-                        const double v = h2[((p * Kz + q) * Kz + r) * Kz + s];
-                        if (!std::isfinite(v)) return fail(h, SPMPS_ERR_BAD_INPUT, "h2 not finite");
-                        if (v == 0.0) continue;
-                        if (p == q && q == r && r == s) { U[p] = v; continue; }
-                        return fail(h, SPMPS_ERR_UNSUPPORTED,
-                                    "two-electron integrals other than (pp|pp) need the general MPO builder");
+                    for (size_t s2 = 0; s2 < Kz; ++s2) {
+                        const double a = h2[((p * Kz + q) * Kz + r) * Kz + s2], b = h2[((q * Kz + p) * Kz + s2) * Kz + r];
+                        if (std::fabs(a - b) > 1e-12 * (1.0 + std::fabs(a)))
+                            return fail(h, SPMPS_ERR_BAD_INPUT, "h2 is not Hermitian: (pq|rs) != (qp|sr)");
                     }
     }
-    return set_ops(h, mpo_nearest_neighbour(K, eps, hop, U, ecore));
+    if (nearest_neighbour_only(K, h1, h2)) {
+        std::vector<double> eps(K), hop(K > 1 ? K - 1 : 0), U(K, 0.0);
+        for (int p = 0; p < K; ++p) eps[p] = h1[p * K + p];
+        for (int p = 0; p + 1 < K; ++p) hop[p] = h1[p * K + p + 1];
+        if (h2) {
+            const size_t Kz = static_cast<size_t>(K);
+            for (size_t p = 0; p < Kz; ++p) U[p] = h2[((p * Kz + p) * Kz + p) * Kz + p];
+        }
+        st = set_ops(h, mpo_nearest_neighbour(K, eps, hop, U, ecore));
+    } else {
+        MPO m;
+        std::string why;
+        if (!mpo_ab_initio(K, h1, h2, ecore, 1 << 20, &m, &why)) return fail(h, SPMPS_ERR_BAD_INPUT, why);
+        if (!mpo_fits(m, h->G + 1, &why)) return fail(h, SPMPS_ERR_UNSUPPORTED, why);
+        st = set_ops(h, std::move(m));
+    }
+    if (st != SPMPS_OK) return st;
+    const size_t Kz = static_cast<size_t>(K);
+    h->ints_h1.assign(h1, h1 + Kz * Kz);
+    if (h2) h->ints_h2.assign(h2, h2 + Kz * Kz * Kz * Kz);
+    else h->ints_h2.clear();
+    h->ints_ecore = ecore;
+    return SPMPS_OK;
+}
+
+spmps_status spmps_set_mpo(spmps_handle h, const int* bond_dims, const double* const* sites) {
+    if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
+    if (!bond_dims || !sites) return fail(h, SPMPS_ERR_BAD_INPUT, "NULL argument");
+    const int K = h->K;
+    if (bond_dims[0] != 1 || bond_dims[K] != 1) return fail(h, SPMPS_ERR_BAD_INPUT, "boundary MPO bonds must have dimension 1");
+    std::vector<int> dims(bond_dims, bond_dims + K + 1);
+    for (int b = 0; b <= K; ++b)
+        if (dims[b] < 1) return fail(h, SPMPS_ERR_BAD_INPUT, "MPO bond dimension < 1");
+    MPO m;
+    m.init(K, dims);
+    for (int k = 0; k < K; ++k) {
+        if (!sites[k]) return fail(h, SPMPS_ERR_BAD_INPUT, "NULL MPO site tensor");
+        for (int wl = 0; wl < dims[k]; ++wl)
+            for (int wr = 0; wr < dims[k + 1]; ++wr) {
+                const double* op = sites[k] + (static_cast<size_t>(wl) * dims[k + 1] + wr) * 16;
+                bool any = false;
+                for (int i = 0; i < 16; ++i) {
+                    if (!std::isfinite(op[i])) return fail(h, SPMPS_ERR_BAD_INPUT, "MPO entry not finite");
+                    any = any || op[i] != 0.0;
+                }
+                if (any) m.add(k, wl, wr, op);
+            }
+    }
+    m.finalize();
+    std::string why;
+    if (!mpo_fits(m, h->G + 1, &why)) return fail(h, SPMPS_ERR_UNSUPPORTED, why);
+    if (!m.finalize_charges(&why)) return fail(h, SPMPS_ERR_BAD_INPUT, why);
+    h->ints_h1.clear();
+    h->ints_h2.clear();
+    h->ints_ecore = 0.0;
+    return set_ops(h, std::move(m));
+}
+
+spmps_status spmps_mpo_from_integrals(int K, const double* h1, const double* h2, double ecore, int* bond_dims,
+                                      double* const* sites) {
+    if (K < 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "need K >= 2");
+    if (!bond_dims) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "bond_dims is NULL");
+    spmps_status st = check_integrals(nullptr, K, h1, h2, ecore);
+    if (st != SPMPS_OK) return st;
+    MPO m;
+    std::string why;
+    if (!mpo_ab_initio(K, h1, h2, ecore, 1 << 20, &m, &why)) return fail(nullptr, SPMPS_ERR_BAD_INPUT, why);
+    for (int b = 0; b <= K; ++b) bond_dims[b] = m.dw[b];
+    if (!sites) return SPMPS_OK;
+    for (int k = 0; k < K; ++k) {
+        if (!sites[k]) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "NULL site pointer");
+        const size_t n = static_cast<size_t>(m.dw[k]) * m.dw[k + 1] * 16;
+        std::fill(sites[k], sites[k] + n, 0.0);
+        for (const auto& e : m.E[k])
+            std::copy(e.op, e.op + 16, sites[k] + (static_cast<size_t>(e.wl) * m.dw[k + 1] + e.wr) * 16);
+    }
+    return SPMPS_OK;
 }
 
 spmps_status spmps_set_mps(spmps_handle h, const int* bond_dims, const int* labels, const double* const* sites,
@@ -1545,6 +1783,13 @@ spmps_status spmps_stats(spmps_handle h, int64_t* counts, double* values) {
         values[1] = h->last_discarded;
         values[2] = h->apply_flops_total;
     }
+    return SPMPS_OK;
+}
+
+spmps_status spmps_davidson_stats(spmps_handle h, int64_t* iterations, int64_t* refine_iterations) {
+    if (!h) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "null handle");
+    if (iterations) *iterations = h->dav_iters;
+    if (refine_iterations) *refine_iterations = h->refine_iters;
     return SPMPS_OK;
 }
 

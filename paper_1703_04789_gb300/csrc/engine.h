@@ -74,6 +74,7 @@ struct EnvStore {
 struct Plan {
     GemmPlan A, C;
     CombPlan B;
+    TilePolicy polA, polC;  // tile policies of phases A and C (autotuned per site, or the default)
     std::vector<int> tileA_rng, tileC_rng, combB_rng;  // [op * G + g] .. [op * G + g + 1]
     std::vector<double> flopsA_rng, flopsB_rng, flopsC_rng;  // algorithmic flops per range
     int64_t t1_size = 0, t2_size = 0;
@@ -113,6 +114,12 @@ struct spmps_t {
     std::vector<double> beta, cg;
 
     bool has_ham = false, has_mps = false;
+    // the integrals of the Hamiltonian (kept for the fragment energies); empty after spmps_set_mpo
+    std::vector<double> ints_h1, ints_h2;
+    double ints_ecore = 0.0;
+    // autotuner: chosen tile candidate per site for phases A and C (-1 = not tuned yet)
+    std::vector<int> tune_a, tune_c;
+    spmps::DevMem tunebuf;
     spmps::OpSet ops;        // H, N
     std::vector<spmps::Bond> bonds;           // K+1
     std::vector<spmps::RowBlockLayout> alay;  // per site, ns = 4

@@ -93,7 +93,20 @@ ColLayout make_col_layout(const Bond& right, int n0, int ns, int sign) {
     return C;
 }
 
-void GemmPlan::add_tiles() {
+TilePolicy tile_candidate(int i) {
+    TilePolicy p;
+    switch (i) {
+        case 1: p.wb_kmin = 32; break;
+        case 2: p.wb_kmin = 128; break;
+        case 3: p.wb_kmin = 1 << 30; break;  // register tiles only
+        case 4: p.wb_mn_max = 1024; break;
+        case 5: p.wb_elems = 128; break;
+        default: break;
+    }
+    return p;
+}
+
+void GemmPlan::add_tiles(const TilePolicy& pol) {
     // register-tiled shapes 0..4 (rows x cols per warp); shape 5 = warp block for long reductions
     static const int shp[5][2] = {{16, 16}, {4, 64}, {64, 4}, {32, 8}, {8, 32}};
     tiles.clear();
@@ -101,9 +114,10 @@ void GemmPlan::add_tiles() {
         const GemmTask& T = tasks[t];
         int64_t ktot = 0;
         for (int q = 0; q < T.nseg; ++q) ktot += segs[T.seg0 + q].K;
-        if (ktot >= 64 && static_cast<int64_t>(T.M) * T.N <= 4096) {
+        if (ktot >= pol.wb_kmin && static_cast<int64_t>(T.M) * T.N <= pol.wb_mn_max) {
             const int tm = T.M < 32 ? T.M : 32;
-            int tn = 256 / tm;
+            int tn = (pol.wb_elems < 256 ? pol.wb_elems : 256) / tm;  // the kernel holds <= 256 outputs
+            if (tn < 1) tn = 1;
             if (tn > 32) tn = 32;
             if (tn > T.N) tn = T.N;
             for (int m0 = 0; m0 < T.M; m0 += tm)
@@ -177,12 +191,10 @@ struct LocalOps {
 };
 
 MPO make_mpo(int K, int dw_bulk) {
+    std::vector<int> dims(K + 1, dw_bulk);
+    dims[0] = dims[K] = 1;
     MPO m;
-    m.K = K;
-    m.dw.assign(K + 1, dw_bulk);
-    m.dw[0] = m.dw[K] = 1;
-    m.W.resize(K);
-    for (int k = 0; k < K; ++k) m.W[k].assign(static_cast<size_t>(m.dw[k]) * m.dw[k + 1] * 16, 0.0);
+    m.init(K, dims);
     return m;
 }
 
@@ -193,11 +205,110 @@ void place(MPO& m, int wl, int wr, const double op[16], double scale, int first,
         int l = wl, r = wr;
         if (k == 0) { if (wl != first) continue; l = 0; }
         if (k == m.K - 1) { if (wr != last) continue; r = 0; }
-        for (int s = 0; s < 4; ++s)
-            for (int t = 0; t < 4; ++t) m.at(k, l, r, s, t) += scale * op[s * 4 + t];
+        m.add(k, l, r, op, scale);
     }
 }
 }  // namespace
+
+void MPO::init(int K_, const std::vector<int>& dims) {
+    K = K_;
+    dw = dims;
+    cn.clear();
+    E.assign(K, {});
+    wr_ptr.assign(K, {});
+    by_wl.assign(K, {});
+    wl_ptr.assign(K, {});
+    pending_.assign(K, {});
+}
+
+void MPO::add(int k, int wl, int wr, const double* op, double scale) {
+    if (pending_.size() != static_cast<size_t>(K)) pending_.assign(K, {});
+    MpoEntry e;
+    e.wl = wl;
+    e.wr = wr;
+    for (int i = 0; i < 16; ++i) e.op[i] = scale * op[i];
+    pending_[k].push_back({(static_cast<uint64_t>(wr) << 32) | static_cast<uint32_t>(wl), static_cast<int>(E[k].size())});
+    E[k].push_back(e);
+}
+
+void MPO::finalize() {
+    if (pending_.size() != static_cast<size_t>(K)) pending_.assign(K, {});
+    for (int k = 0; k < K; ++k) {
+        auto& pend = pending_[k];
+        // stable order by (wr, wl), then merge duplicates
+        std::stable_sort(pend.begin(), pend.end(),
+                         [](const std::pair<uint64_t, int>& a, const std::pair<uint64_t, int>& b) { return a.first < b.first; });
+        std::vector<MpoEntry> out;
+        out.reserve(E[k].size());
+        if (pend.empty()) {
+            // already finalized once (or built without add): re-sort the stored entries
+            std::vector<MpoEntry> cur = E[k];
+            std::stable_sort(cur.begin(), cur.end(), [](const MpoEntry& a, const MpoEntry& b) {
+                return a.wr != b.wr ? a.wr < b.wr : a.wl < b.wl;
+            });
+            for (const auto& e : cur) {
+                if (!out.empty() && out.back().wl == e.wl && out.back().wr == e.wr) {
+                    for (int i = 0; i < 16; ++i) out.back().op[i] += e.op[i];
+                } else {
+                    out.push_back(e);
+                }
+            }
+        } else {
+            for (size_t i = 0; i < pend.size(); ++i) {
+                const MpoEntry& e = E[k][pend[i].second];
+                if (!out.empty() && out.back().wl == e.wl && out.back().wr == e.wr) {
+                    for (int q = 0; q < 16; ++q) out.back().op[q] += e.op[q];
+                } else {
+                    out.push_back(e);
+                }
+            }
+        }
+        // drop all-zero entries
+        std::vector<MpoEntry> nz;
+        nz.reserve(out.size());
+        for (const auto& e : out) {
+            bool any = false;
+            for (double v : e.op) any = any || v != 0.0;
+            if (any) nz.push_back(e);
+        }
+        E[k].swap(nz);
+        pend.clear();
+        pend.shrink_to_fit();
+        // indices
+        const int dr = dw[k + 1], dl = dw[k];
+        wr_ptr[k].assign(dr + 1, 0);
+        for (const auto& e : E[k]) ++wr_ptr[k][e.wr + 1];
+        for (int u = 0; u < dr; ++u) wr_ptr[k][u + 1] += wr_ptr[k][u];
+        by_wl[k].resize(E[k].size());
+        for (size_t i = 0; i < E[k].size(); ++i) by_wl[k][i] = static_cast<int>(i);
+        std::stable_sort(by_wl[k].begin(), by_wl[k].end(), [&](int a, int b) {
+            const MpoEntry& x = E[k][a];
+            const MpoEntry& y = E[k][b];
+            return x.wl != y.wl ? x.wl < y.wl : x.wr < y.wr;
+        });
+        wl_ptr[k].assign(dl + 1, 0);
+        for (const auto& e : E[k]) ++wl_ptr[k][e.wl + 1];
+        for (int w = 0; w < dl; ++w) wl_ptr[k][w + 1] += wl_ptr[k][w];
+    }
+}
+
+double MPO::get(int k, int wl, int wr, int s, int t) const {
+    const auto& v = E[k];
+    int lo = wr_ptr[k][wr], hi = wr_ptr[k][wr + 1];
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (v[mid].wl < wl) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < wr_ptr[k][wr + 1] && v[lo].wl == wl) return v[lo].op[s * 4 + t];
+    return 0.0;
+}
+
+size_t MPO::entries() const {
+    size_t n = 0;
+    for (const auto& v : E) n += v.size();
+    return n;
+}
 
 bool MPO::finalize_charges(std::string* err) {
     cn.assign(K + 1, {});
@@ -205,26 +316,37 @@ bool MPO::finalize_charges(std::string* err) {
     std::vector<std::vector<char>> seen(K + 1);
     for (int b = 0; b <= K; ++b) seen[b].assign(dw[b], 0);
     seen[0][0] = 1;
+    bool pruned = false;
     for (int k = 0; k < K; ++k) {
-        for (int wl = 0; wl < dw[k]; ++wl)
-            for (int wr = 0; wr < dw[k + 1]; ++wr)
-                for (int s = 0; s < 4; ++s)
-                    for (int t = 0; t < 4; ++t) {
-                        if (get(k, wl, wr, s, t) == 0.0) continue;
-                        int c = cn[k][wl] + kLocalN[s] - kLocalN[t];
-                        if (!seen[k + 1][wr]) {
-                            seen[k + 1][wr] = 1;
-                            cn[k + 1][wr] = c;
-                        } else if (cn[k + 1][wr] != c) {
-                            if (err) *err = "MPO does not conserve particle number";
-                            return false;
-                        }
+        // entries leaving a channel that no nonzero path from the left boundary reaches cannot
+        // contribute (their left environment vanishes): drop them
+        std::vector<MpoEntry> live;
+        live.reserve(E[k].size());
+        for (const auto& e : E[k])
+            if (seen[k][e.wl]) live.push_back(e);
+        if (live.size() != E[k].size()) {
+            E[k].swap(live);
+            pruned = true;
+        }
+        for (const auto& e : E[k])
+            for (int s = 0; s < 4; ++s)
+                for (int t = 0; t < 4; ++t) {
+                    if (e.op[s * 4 + t] == 0.0) continue;
+                    const int c = cn[k][e.wl] + kLocalN[s] - kLocalN[t];
+                    if (!seen[k + 1][e.wr]) {
+                        seen[k + 1][e.wr] = 1;
+                        cn[k + 1][e.wr] = c;
+                    } else if (cn[k + 1][e.wr] != c) {
+                        if (err) *err = "MPO does not conserve particle number";
+                        return false;
                     }
+                }
     }
     if (cn[K][0] != 0) {
         if (err) *err = "MPO changes the particle number";
         return false;
     }
+    if (pruned) finalize();  // rebuild the per-wr / per-wl indices
     return true;
 }
 
@@ -244,9 +366,8 @@ MPO mpo_nearest_neighbour(int K, const std::vector<double>& eps, const std::vect
         matmul4(o.n_a, o.n_b, tmp);
         for (int i = 0; i < 16; ++i) local[i] = U[k] * tmp[i] + eps[k] * (o.n_a[i] + o.n_b[i]);
         if (k == 0) for (int i = 0; i < 16; ++i) local[i] += ecore * o.I[i];
-        const int l = k == 0 ? 0 : 0, r = k == K - 1 ? 0 : 5;
-        for (int s = 0; s < 4; ++s)
-            for (int t = 0; t < 4; ++t) m.at(k, l, r, s, t) += local[s * 4 + t];
+        const int l = 0, r = k == K - 1 ? 0 : 5;
+        m.add(k, l, r, local);
     }
     for (int k = 0; k + 1 < K; ++k) {
         // opening legs on site k, closing legs (times hop_k) on site k+1
@@ -260,14 +381,12 @@ MPO mpo_nearest_neighbour(int K, const std::vector<double>& eps, const std::vect
         opens[0] = oa; opens[1] = ob; opens[2] = oc; opens[3] = od;
         const double* closes[4] = {o.c_a, o.c_b, o.cdag_a, o.cdag_b};
         for (int c = 0; c < 4; ++c) {
-            for (int s = 0; s < 4; ++s)
-                for (int t = 0; t < 4; ++t) {
-                    m.at(k, l, r_open[c], s, t) += opens[c][s * 4 + t];
-                    const int rr = k + 1 == K - 1 ? 0 : 5;
-                    m.at(k + 1, r_open[c], rr, s, t) += hop[k] * closes[c][s * 4 + t];
-                }
+            m.add(k, l, r_open[c], opens[c]);
+            const int rr = k + 1 == K - 1 ? 0 : 5;
+            m.add(k + 1, r_open[c], rr, closes[c], hop[k]);
         }
     }
+    m.finalize();
     return m;
 }
 
@@ -299,6 +418,7 @@ MPO mpo_s2(int K) {
     place(m, 3, 3, o.I, 1.0, 0, 4);
     place(m, 3, 4, szz, 1.0, 0, 4);
     place(m, 4, 4, o.I, 1.0, 0, 4);
+    m.finalize();
     return m;
 }
 
@@ -306,6 +426,7 @@ MPO mpo_identity(int K) {
     static const LocalOps o;
     MPO m = make_mpo(K, 1);
     place(m, 0, 0, o.I, 1.0, 0, 0);
+    m.finalize();
     return m;
 }
 
@@ -326,14 +447,16 @@ MPO mpo_rotated(const MPO& m, double beta) {
     site_rotation(beta, r);
     MPO out = m;
     for (int k = 0; k < m.K; ++k)
-        for (int wl = 0; wl < m.dw[k]; ++wl)
-            for (int wr = 0; wr < m.dw[k + 1]; ++wr)
-                for (int s = 0; s < 4; ++s)
-                    for (int t = 0; t < 4; ++t) {
-                        double acc = 0.0;
-                        for (int u = 0; u < 4; ++u) acc += m.get(k, wl, wr, s, u) * r[u * 4 + t];
-                        out.at(k, wl, wr, s, t) = acc;
-                    }
+        for (auto& e : out.E[k]) {
+            double tmp[16];
+            for (int s = 0; s < 4; ++s)
+                for (int t = 0; t < 4; ++t) {
+                    double acc = 0.0;
+                    for (int u = 0; u < 4; ++u) acc += e.op[s * 4 + u] * r[u * 4 + t];
+                    tmp[s * 4 + t] = acc;
+                }
+            for (int i = 0; i < 16; ++i) e.op[i] = tmp[i];
+        }
     return out;
 }
 

@@ -521,100 +521,24 @@ __global__ void __launch_bounds__(256) k_ritz(const double* __restrict__ h, cons
     }
 }
 
-// ---- incremental Ritz step (one warp) ---------------------------------------------------------
+// ---- incremental Ritz step --------------------------------------------------------------------
 // Keeps, across the iterations of one Davidson solve, an n-orthonormal coefficient basis X
 // (Y = V X has Y^T N Y = I), the projected matrix hp = X^T h X and the eigenvectors C of hp.
 // Adding basis vector v_m: classical Gram-Schmidt of e_m against X in the n inner product,
 // twice; the direction is kept when its n-norm^2 exceeds eps * max(diag n) (numerically null
 // directions of the metric are dropped, as in canonical orthogonalisation).  hp grows by one row
-// and column; its eigenproblem is re-solved by warp-level cyclic Jacobi started from the previous
+// and column; its eigenproblem is re-solved by block-level cyclic Jacobi started from the previous
 // eigenvectors, so only the new coupling has to be rotated away.
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__device__ int warp_jacobi(double* A, double* V, int n, int lane, int max_sweeps, double* cs, int* pq) {
-    constexpr int R = RitzState::kR;
-    for (int e = lane; e < n * n; e += 32) {
-        const int i = e / n, j = e - i * n;
-        V[i * R + j] = i == j ? 1.0 : 0.0;
-    }
-    __syncwarp();
-    if (n <= 1) return 0;
-    const int np = (n + 1) & ~1, half = np / 2;
-    int sweep = 0;
-    double off_prev = INFINITY;
-    for (; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int e = lane; e < n * n; e += 32) {
-            const int i = e / n, j = e - i * n;
-            const double v = A[i * R + j];
-            tot += v * v;
-            if (i != j) off += v * v;
-        }
-        off = warp_sum(off);
-        tot = warp_sum(tot);
-        // converged, or near convergence and at the rounding-noise floor
-        if (off <= 1e-28 * tot || off == 0.0 || (off <= 1e-20 * tot && off > 0.25 * off_prev)) break;
-        off_prev = off;
-        const double tiny = 1e-18 * sqrt(tot);
-        for (int round = 0; round < np - 1; ++round) {
-            if (lane < half) {
-                auto player = [&](int k) { return k == 0 ? 0 : 1 + ((k - 1 + round) % (np - 1)); };
-                int p = player(lane), q = player(np - 1 - lane);
-                if (p > q) { const int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0;
-                if (q < n) {
-                    const double apq = A[p * R + q];
-                    if (fabs(apq) > tiny) {
-                        const double theta = (A[q * R + q] - A[p * R + p]) / (2.0 * apq);
-                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        s = t * c;
-                    } else {
-                        q = -1;
-                    }
-                } else {
-                    q = -1;
-                }
-                pq[2 * lane] = p;
-                pq[2 * lane + 1] = q;
-                cs[2 * lane] = c;
-                cs[2 * lane + 1] = s;
-            }
-            __syncwarp();
-            for (int e = lane; e < half * n; e += 32) {
-                const int i = e / n, j = e - i * n;
-                const int p = pq[2 * i], q = pq[2 * i + 1];
-                if (q < 0) continue;
-                const double c = cs[2 * i], s = cs[2 * i + 1];
-                const double ap = A[p * R + j], aq = A[q * R + j];
-                A[p * R + j] = c * ap - s * aq;
-                A[q * R + j] = s * ap + c * aq;
-            }
-            __syncwarp();
-            for (int e = lane; e < half * n; e += 32) {
-                const int i = e / n, j = e - i * n;
-                const int p = pq[2 * i], q = pq[2 * i + 1];
-                if (q < 0) continue;
-                const double c = cs[2 * i], s = cs[2 * i + 1];
-                const double ap = A[j * R + p], aq = A[j * R + q];
-                A[j * R + p] = c * ap - s * aq;
-                A[j * R + q] = s * ap + c * aq;
-                const double vp = V[j * R + p], vq = V[j * R + q];
-                V[j * R + p] = c * vp - s * vq;
-                V[j * R + q] = s * vp + c * vq;
-            }
-            __syncwarp();
-        }
-    }
-    return sweep;
-}
-
-__global__ void __launch_bounds__(32) k_ritz_inc(const double* __restrict__ h, const double* __restrict__ nm, int ldm,
-                                                 int m, int reset, double eps, RitzState* __restrict__ st,
-                                                 double* __restrict__ coef, double* __restrict__ scal) {
+// Incremental Ritz step (one CTA of 128 threads: one warp per SM sub-partition, so the FP64
+// products and the Jacobi sweeps use all four FP64 pipes of the SM).
+__global__ void __launch_bounds__(128) k_ritz_inc(const double* __restrict__ h, const double* __restrict__ nm, int ldm,
+                                                  int m, int reset, double eps, RitzState* __restrict__ st,
+                                                  double* __restrict__ coef, double* __restrict__ scal) {
     constexpr int R = RitzState::kR;
     extern __shared__ double rs_smem[];
     double* X = rs_smem;           // n-orthonormal coefficient basis, X[i + j*R]
@@ -624,104 +548,112 @@ __global__ void __launch_bounds__(32) k_ritz_inc(const double* __restrict__ h, c
     double* T = A + R * R;
     double* NS = T + R * R;        // n, full symmetric, NS[i*R + j]
     double* HS = NS + R * R;       // h, full symmetric
-    __shared__ double cs[R + 2];
-    __shared__ int pq[R + 2];
-    const int lane = threadIdx.x;
+    __shared__ double cs_sh[R + 2], red_sh[40];
+    __shared__ int pq_sh[R + 2];
+    __shared__ int k_sh;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     int k = 0, m0 = 0, kc = 0;
     if (!reset) {
         k = st->k;
         m0 = st->m;
         kc = st->kc;
-        for (int e = lane; e < R * R; e += 32) {
+        for (int e = tid; e < R * R; e += nt) {
             X[e] = st->X[e];
             HP[e] = st->hp[e];
             CC[e] = st->C[e];
         }
     }
-    for (int e = lane; e < m * m; e += 32) {
+    for (int e = tid; e < m * m; e += nt) {
         const int i = e / m, j = e - i * m;
         const int hi = i > j ? i : j, lo = i > j ? j : i;
         NS[i * R + j] = nm[hi * ldm + lo];
         HS[i * R + j] = h[hi * ldm + lo];
     }
-    __syncwarp();
-    double dmax = 0.0;
-    for (int i = 0; i < m; ++i) dmax = fmax(dmax, NS[i * R + i]);
-    for (int col = m0; col < m; ++col) {
-        // y = e_col - X (X^T n y), twice, in the n inner product (lane i holds y_i, i <= col)
-        double y = lane == col ? 1.0 : 0.0;
-        for (int pass = 0; pass < 2; ++pass) {
+    __syncthreads();
+    // new columns of the n-orthonormal basis (32-long vectors: warp 0)
+    if (tid < 32) {
+        double dmax = 0.0;
+        for (int i = 0; i < m; ++i) dmax = fmax(dmax, NS[i * R + i]);
+        for (int col = m0; col < m; ++col) {
+            // y = e_col - X (X^T n y), twice, in the n inner product (lane i holds y_i, i <= col)
+            double y = lane == col ? 1.0 : 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                double ny = 0.0;
+                for (int l = 0; l <= col; ++l) {
+                    const double yl = __shfl_sync(0xffffffffu, y, l);
+                    if (lane <= col) ny = fma(NS[lane * R + l], yl, ny);
+                }
+                double corr = 0.0;
+                for (int j = 0; j < k; ++j) {
+                    const double cj = warp_sum(lane <= col ? X[lane + j * R] * ny : 0.0);
+                    if (lane <= col) corr = fma(X[lane + j * R], cj, corr);
+                }
+                y -= corr;
+            }
             double ny = 0.0;
             for (int l = 0; l <= col; ++l) {
                 const double yl = __shfl_sync(0xffffffffu, y, l);
                 if (lane <= col) ny = fma(NS[lane * R + l], yl, ny);
             }
-            double corr = 0.0;
-            for (int j = 0; j < k; ++j) {
-                const double cj = warp_sum(lane <= col ? X[lane + j * R] * ny : 0.0);
-                if (lane <= col) corr = fma(X[lane + j * R], cj, corr);
+            const double nu2 = warp_sum(lane <= col ? y * ny : 0.0);
+            if (nu2 > eps * dmax && nu2 > 0.0) {
+                const double inv = 1.0 / sqrt(nu2);
+                X[lane + k * R] = lane <= col ? y * inv : 0.0;
+                __syncwarp();
+                double hx = 0.0;
+                for (int l = 0; l <= col; ++l)
+                    if (lane <= col) hx = fma(HS[lane * R + l], X[l + k * R], hx);
+                for (int j = 0; j <= k; ++j) {
+                    const double v = warp_sum(lane <= col ? X[lane + j * R] * hx : 0.0);
+                    if (lane == 0) { HP[j * R + k] = v; HP[k * R + j] = v; }
+                }
+                ++k;
             }
-            y -= corr;
-        }
-        double ny = 0.0;
-        for (int l = 0; l <= col; ++l) {
-            const double yl = __shfl_sync(0xffffffffu, y, l);
-            if (lane <= col) ny = fma(NS[lane * R + l], yl, ny);
-        }
-        const double nu2 = warp_sum(lane <= col ? y * ny : 0.0);
-        if (nu2 > eps * dmax && nu2 > 0.0) {
-            const double inv = 1.0 / sqrt(nu2);
-            X[lane + k * R] = lane <= col ? y * inv : 0.0;
             __syncwarp();
-            double hx = 0.0;
-            for (int l = 0; l <= col; ++l)
-                if (lane <= col) hx = fma(HS[lane * R + l], X[l + k * R], hx);
-            for (int j = 0; j <= k; ++j) {
-                const double v = warp_sum(lane <= col ? X[lane + j * R] * hx : 0.0);
-                if (lane == 0) { HP[j * R + k] = v; HP[k * R + j] = v; }
-            }
-            ++k;
         }
-        __syncwarp();
+        if (lane == 0) k_sh = k;
     }
+    __syncthreads();
+    k = k_sh;
     // W = previous eigenvectors padded with the identity (in T), A = W^T HP W
-    for (int e = lane; e < k * k; e += 32) {
+    for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e - i * k;
         T[i * R + j] = (i < kc && j < kc) ? CC[i * R + j] : (i == j ? 1.0 : 0.0);
     }
-    __syncwarp();
-    for (int e = lane; e < k * k; e += 32) {  // A = HP W
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {  // A = HP W
         const int i = e / k, j = e - i * k;
         double acc = 0.0;
         for (int l = 0; l < k; ++l) acc = fma(HP[i * R + l], T[l * R + j], acc);
         A[i * R + j] = acc;
     }
-    __syncwarp();
-    for (int e = lane; e < k * k; e += 32) {  // CC = W^T (HP W)  (CC is free: W holds the old C)
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {  // CC = W^T (HP W)  (CC is free: W holds the old C)
         const int i = e / k, j = e - i * k;
         double acc = 0.0;
         for (int l = 0; l < k; ++l) acc = fma(T[l * R + i], A[l * R + j], acc);
         CC[i * R + j] = acc;
     }
-    __syncwarp();
-    for (int e = lane; e < k * k; e += 32) {  // A = symmetrised W^T HP W
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {  // A = symmetrised W^T HP W
         const int i = e / k, j = e - i * k;
         A[i * R + j] = 0.5 * (CC[i * R + j] + CC[j * R + i]);
     }
-    __syncwarp();
-    warp_jacobi(A, CC, k, lane, 40, cs, pq);  // CC = rotations
+    __syncthreads();
+    jacobi_cta(A, R, CC, R, k, 40, cs_sh, pq_sh, red_sh);  // CC = rotations
+    __syncthreads();
     // new eigenvectors W * rotations, into NS (free now), then back to CC
-    for (int e = lane; e < k * k; e += 32) {
+    for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e - i * k;
         double acc = 0.0;
         for (int l = 0; l < k; ++l) acc = fma(T[i * R + l], CC[l * R + j], acc);
         NS[i * R + j] = acc;
     }
-    __syncwarp();
+    __syncthreads();
     int jmin = 0;
     for (int i = 1; i < k; ++i)
         if (A[i * R + i] < A[jmin * R + jmin]) jmin = i;
-    for (int e = lane; e < R * R; e += 32) {
+    for (int e = tid; e < R * R; e += nt) {
         const int i = e / R, j = e - i * R;
         const double c = (i < k && j < k) ? NS[i * R + j] : 0.0;
         CC[e] = c;
@@ -729,18 +661,18 @@ __global__ void __launch_bounds__(32) k_ritz_inc(const double* __restrict__ h, c
         st->X[e] = X[e];
         st->hp[e] = HP[e];
     }
-    __syncwarp();
-    if (lane == 0) {
+    __syncthreads();
+    if (tid == 0) {
         st->k = k;
         st->m = m;
         st->kc = k;
         scal[0] = k > 0 ? A[jmin * R + jmin] : 0.0;
         scal[1] = static_cast<double>(k);
     }
-    if (lane < m) {
+    if (tid < m) {
         double acc = 0.0;
-        for (int j = 0; j < k; ++j) acc = fma(X[lane + j * R], CC[j * R + jmin], acc);
-        coef[lane] = k > 0 ? acc : 0.0;
+        for (int j = 0; j < k; ++j) acc = fma(X[tid + j * R], CC[j * R + jmin], acc);
+        coef[tid] = k > 0 ? acc : 0.0;
     }
 }
 
@@ -1007,7 +939,7 @@ cudaError_t launch_ritz_inc(const double* h, const double* nmat, int ldm, int m,
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
-    k_ritz_inc<<<1, 32, smem, st>>>(h, nmat, ldm, m, reset, eps_metric, state, coef, scal);
+    k_ritz_inc<<<1, 128, smem, st>>>(h, nmat, ldm, m, reset, eps_metric, state, coef, scal);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ cudaError_t launch_basis_rotate(const double* src, int64_t ld, int m, const doub
 cudaError_t launch_ritz(const double* h, const double* nmat, int ldm, int m, double eps_metric, double* coef,
                         double* scal, cudaStream_t st);
 
-// Incremental Ritz step (one warp): state kept across iterations of one solve; reset != 0
+// Incremental Ritz step (one CTA of 128 threads): state kept across iterations of one solve; reset != 0
 // rebuilds it from the m stored columns.  Same outputs as launch_ritz.
 struct RitzState {
     static constexpr int kR = 32;

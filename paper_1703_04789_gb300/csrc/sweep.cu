@@ -122,33 +122,25 @@ spmps_status metric_cg(spmps_t* h, int k, DavBuffers& B, int64_t n, const double
 // Lowest generalised eigenpair at sites (k, k+1), starting from the device vector x0 (n).
 // On return B.x holds x with x^T N x = 1.  tol_r / tol_theta / cap are this stage's criteria.
 spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out, double tol_r,
-                            double tol_theta, int cap);
+                            double tol_theta, int cap, double switch_tol);
 
 spmps_status davidson(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out) {
     if (h->opt.precision == 0) {
         h->apply_precision = 0;
-        return davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter);
+        return davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter, 0.0);
     }
-    // reduced-precision stage (tensor-core H_eff x), then FP64 refinement from its vector
-    const double tol1 = h->opt.precision == 1 ? 1e-3 : 1e-5;
+    // reduced-precision H_eff x (tensor cores) until |r| < switch_tol, then the basis products are
+    // recomputed in FP64 and the same solve continues in FP64 to the final criteria
+    const double switch_tol = std::max(h->opt.precision == 1 ? 1e-3 : 1e-5, h->opt.dav_tol_r);
     h->apply_precision = h->opt.precision;
-    DavidsonOut o1;
-    spmps_status st = davidson_stage(h, k, x0, B, &o1, std::max(tol1, h->opt.dav_tol_r), 1e-7, h->opt.dav_max_iter);
+    spmps_status st = davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter,
+                                     switch_tol);
     h->apply_precision = 0;
-    if (st != SPMPS_OK) return st;
-    DevMem xs;
-    const int64_t n = x_size(h, k);
-    CK(xs.ensure(std::max<int64_t>(n, 1) * sizeof(double)));
-    CK(cudaMemcpyAsync(xs.p, B.x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    const int64_t it0 = h->dav_iters;
-    st = davidson_stage(h, k, xs.as<double>(), B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter);
-    h->refine_iters += h->dav_iters - it0;
-    out->iters += o1.iters;
     return st;
 }
 
 spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out, double tol_r,
-                            double tol_theta, int cap) {
+                            double tol_theta, int cap, double switch_tol) {
     const int64_t n = x_size(h, k);
     const int ms = h->opt.dav_max_sub;
     spmps_status st = ensure_dav(h, B, n, ms);
@@ -178,6 +170,28 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
     int m = 1;
     int reset = 1;  // rebuild the incremental Ritz state from the stored columns
     double theta_prev = INFINITY;
+    bool switched = !(switch_tol > 0.0);  // FP64 action from here on
+    int switch_it = 0;
+    // the reduced-precision action has a noise floor: switch also when |r| has not improved on its
+    // best value by 10 % for kStagnation iterations
+    constexpr int kStagnation = 12;
+    double best_rn = INFINITY;
+    int best_it = 0;
+    // recompute H V and N V of the stored basis in FP64 and rebuild the subspace matrices
+    auto switch_to_fp64 = [&](int it_now) -> spmps_status {
+        h->apply_precision = 0;
+        for (int j2 = 0; j2 < m; ++j2) {
+            spmps_status s2 = apply_column(h, k, B, n, j2);
+            if (s2 != SPMPS_OK) return s2;
+            s2 = subspace_column(h, B, n, ms, j2);
+            if (s2 != SPMPS_OK) return s2;
+        }
+        switched = true;
+        switch_it = it_now;
+        reset = 1;
+        theta_prev = INFINITY;
+        return SPMPS_OK;
+    };
     // harvesting of (features, error direction) pairs for the learned correction
     MlpState& ML = h->mlp;
     const bool harvest = ML.harvest && ML.count < ML.capacity;
@@ -306,11 +320,21 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         out->theta = theta;
         out->resid = rn;
         out->iters = it;
-        if (rn < tol_r && std::fabs(theta - theta_prev) < tol_theta) {
+        if (switched && rn < tol_r && std::fabs(theta - theta_prev) < tol_theta) {
             out->converged = true;
+            h->refine_iters += switch_it > 0 ? it - switch_it : 0;
             return finish_harvest();
         }
         theta_prev = theta;
+        if (rn < 0.9 * best_rn) {
+            best_rn = rn;
+            best_it = it;
+        }
+        if (!switched && (rn < switch_tol || it - best_it >= kStagnation)) {
+            // the new direction (column m) is applied in FP64 below
+            st = switch_to_fp64(it);
+            if (st != SPMPS_OK) return st;
+        }
         if (!(host[3] > 1e-28)) {
             // the correction lies in the basis: fall back to the diagonal correction (after a
             // learned one), then to the residual itself
@@ -325,7 +349,16 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
                 st = orthogonalise(h, B, n, m, tcol, &nrm2);
                 if (st != SPMPS_OK) return st;
             }
-            if (!(nrm2 > 1e-28)) return finish_harvest();  // the basis spans the reachable space
+            if (!(nrm2 > 1e-28)) {
+                // the basis spans the reachable space: finish in FP64
+                if (!switched) {
+                    st = switch_to_fp64(it);
+                    if (st != SPMPS_OK) return st;
+                    continue;
+                }
+                h->refine_iters += switch_it > 0 ? it - switch_it : 0;
+                return finish_harvest();
+            }
             CK(launch_scale_inv_sqrt(tcol, n, sc + 3, h->stream));
             ++h->launches;
         }
@@ -335,6 +368,7 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         if (st != SPMPS_OK) return st;
         ++m;
     }
+    h->refine_iters += switch_it > 0 ? cap - switch_it : 0;
     return finish_harvest();
 }
 
@@ -785,6 +819,7 @@ spmps_status spmps_sweep(spmps_handle h, int n_sweeps, double* energies) {
     DevMem x0;
     bool all_converged = true;
     h->dav_iters = 0;
+    h->refine_iters = 0;
     double disc_total = 0.0;
     for (int sw = 0; sw < n_sweeps; ++sw) {
         double theta = 0.0;
