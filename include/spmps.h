@@ -53,7 +53,9 @@ typedef struct {
     int batched;        /* 1: one grouped launch per contraction phase over all beta points and
                            blocks (default); 0: one launch per beta point and phase          */
     int precond;        /* Davidson correction: 0 = diagonal (default), 1 = metric CG,
-                           2 = learned (spmps_mlp_*; the diagonal correction is its fallback) */
+                           2 = learned (spmps_mlp_*; the diagonal correction is its fallback),
+                           3 = Olsen: the diagonal correction plus eps M^-1 N x with eps making
+                           it N-orthogonal to x (M = diag H - theta diag N) */
     int cg_steps;       /* CG steps on N_eff t = r for precond == 1 (default 5)               */
     double dav_tol_r;   /* Davidson residual norm tolerance (default 1e-6)                    */
     double dav_tol_theta; /* Davidson eigenvalue change tolerance (default 1e-10)             */

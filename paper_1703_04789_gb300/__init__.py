@@ -126,7 +126,7 @@ class Spmps:
         o = Options()
         self.lib.spmps_default_options(C.byref(o))
         o.batched = 1 if batched else 0
-        o.precond = {"diag": 0, "metric": 1, "learned": 2}[precond]
+        o.precond = {"diag": 0, "metric": 1, "learned": 2, "olsen": 3}[precond]
         o.cg_steps, o.dav_tol_r, o.dav_tol_theta = cg_steps, dav_tol_r, dav_tol_theta
         o.dav_max_sub, o.dav_max_iter, o.device = dav_max_sub, dav_max_iter, device
         o.jacobi_smem_max = jacobi_smem_max

@@ -95,6 +95,7 @@ spmps_status env_boundary(spmps_t* h, EnvStore& E, int bond) {
     CK(cudaMemcpyAsync(E.buf.p, ones.data(), E.total * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     E.valid = true;
+    E.version = ++h->env_counter;
     return SPMPS_OK;
 }
 
@@ -222,7 +223,13 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
             out[r] = static_cast<int>(t);
         }
     };
-    std::vector<int> a_task_rng = P.tileA_rng, c_task_rng = P.tileC_rng;
+    if (!P.task_rng_kept) {
+        P.taskA_rng = P.tileA_rng;
+        P.taskC_rng = P.tileC_rng;
+        P.task_rng_kept = true;
+    }
+    const std::vector<int>& a_task_rng = P.taskA_rng;
+    const std::vector<int>& c_task_rng = P.taskC_rng;
     auto task_flops = [](const GemmPlan& gp, const std::vector<int>& rng, std::vector<double>& out) {
         out.assign(rng.size(), 0.0);
         for (size_t r = 0; r + 1 < rng.size(); ++r)
@@ -248,7 +255,8 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
 
 // Run the three phases for the (op, g) ranges [r0, r1) (all of them when batched).  When ev
 // is given, events ev[0..4] are recorded around the zero fill and the phases.
-spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t st, cudaEvent_t* ev) {
+spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t st, cudaEvent_t* ev,
+                      const SlotsF* split) {
     const bool batched = h->opt.batched != 0;
     if (ev) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(S.p[3], 0, std::max<int64_t>(1, P.t1_size) * sizeof(double), st));
@@ -270,10 +278,16 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
             const int t0 = rng[lo], t1 = rng[hi];
             ++h->launches;
             const int rec = h->profile ? prof_begin(h, st, 0, range_flops(fl, lo, hi)) : -1;
-            cudaError_t e = tf ? launch_gemm_tf32(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
-                                                  cmaps.as<int>(), t1 - t0, tf == 2, st)
-                               : launch_gemm_f64(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
-                                                 cmaps.as<int>(), t1 - t0, st);
+            cudaError_t e;
+            if (tf && split)
+                e = launch_gemm_tf32s(S, *split, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
+                                      cmaps.as<int>(), t1 - t0, tf == 2, st);
+            else if (tf)
+                e = launch_gemm_tf32(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
+                                     cmaps.as<int>(), t1 - t0, tf == 2, st);
+            else
+                e = launch_gemm_f64(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
+                                    cmaps.as<int>(), t1 - t0, st);
             if (rec >= 0) prof_end(h, st, rec);
             return e;
         };
@@ -296,16 +310,29 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
     auto runC = [&](int a, int b) -> cudaError_t {
         return gemm(P.d_tasksC, P.d_segsC, P.d_tilesC, P.d_cmapsC, P.tileC_rng, P.flopsC_rng, a, b);
     };
+    // tensor-core phases read pre-split operands: x before phase A, the phase-B output before C
+    const bool pre_split = prec > 0 && split && r0 < G;
+    if (pre_split) {
+        CK(launch_split_tf32(S.p[0], P.reduce_nx, split->p[0], st));
+        ++h->launches;
+    }
+    auto split_t3 = [&]() -> cudaError_t {
+        if (!pre_split) return cudaSuccess;
+        ++h->launches;
+        return launch_split_tf32(S.p[4], P.t2_size, split->p[4], st);
+    };
     if (batched) {
         CK(runA(r0, r1));
         if (ev) CK(cudaEventRecord(ev[2], st));
         CK(runB(r0, r1));
+        CK(split_t3());
         if (ev) CK(cudaEventRecord(ev[3], st));
         CK(runC(r0, r1));
     } else {
         for (int r = r0; r < r1; ++r) CK(runA(r, r + 1));
         if (ev) CK(cudaEventRecord(ev[2], st));
         for (int r = r0; r < r1; ++r) CK(runB(r, r + 1));
+        CK(split_t3());
         if (ev) CK(cudaEventRecord(ev[3], st));
         for (int r = r0; r < r1; ++r) CK(runC(r, r + 1));
     }
@@ -331,6 +358,7 @@ void build_left_plan(spmps_t* h, int i, const EnvStore& Lo, const EnvStore& Ln, 
     const int G = h->G, nops = h->ops.n_ops();
     const int ngl = static_cast<int>(bl.groups.size()), ngr = static_cast<int>(br.groups.size());
     P.A.clear(); P.B.clear(); P.C.clear();
+    P.task_rng_kept = false;
     P.tileA_rng.assign(nops * G + 1, 0);
     P.tileC_rng.assign(nops * G + 1, 0);
     P.combB_rng.assign(nops * G + 1, 0);
@@ -500,6 +528,7 @@ void build_right_plan(spmps_t* h, int i, const EnvStore& Ro, const EnvStore& Rn,
     const int G = h->G, nops = h->ops.n_ops();
     const int ngl = static_cast<int>(bl.groups.size()), ngr = static_cast<int>(br.groups.size());
     P.A.clear(); P.B.clear(); P.C.clear();
+    P.task_rng_kept = false;
     P.tileA_rng.assign(nops * G + 1, 0);
     P.tileC_rng.assign(nops * G + 1, 0);
     P.combB_rng.assign(nops * G + 1, 0);
@@ -663,6 +692,7 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
     const int G = h->G, nops = h->ops.n_ops();
     const int ngl = static_cast<int>(bl.groups.size()), ngr = static_cast<int>(br.groups.size());
     P.A.clear(); P.B.clear(); P.C.clear();
+    P.task_rng_kept = false;
     P.diag_blocks.clear();
     P.diag_terms.clear();
     P.tileA_rng.assign(nops * G + 1, 0);
@@ -979,6 +1009,7 @@ spmps_status update_left(spmps_t* h, int i) {
     if (st != SPMPS_OK) return st;
     CK(cudaStreamSynchronize(h->stream));  // plan buffers are freed on return
     Ln.valid = true;
+    Ln.version = ++h->env_counter;
     return SPMPS_OK;
 }
 
@@ -1012,6 +1043,7 @@ spmps_status update_right(spmps_t* h, int i) {
     if (st != SPMPS_OK) return st;
     CK(cudaStreamSynchronize(h->stream));
     Rn.valid = true;
+    Rn.version = ++h->env_counter;
     return SPMPS_OK;
 }
 
@@ -1055,6 +1087,12 @@ spmps_status tune_apply_plan(spmps_t* h, int k, Plan& P) {
         h->tune_c.assign(h->K, -1);
     }
     if (h->tune_a[k] < 0) {
+        struct Prec {  // tune with the FP64 kernels whatever the solver stage
+            spmps_t* h;
+            int saved;
+            ~Prec() { h->apply_precision = saved; }
+        } prec{h, h->apply_precision};
+        h->apply_precision = 0;
         const int64_t nx = std::max<int64_t>(1, P.reduce_nx);
         CK(h->tunebuf.ensure(3 * nx * sizeof(double)));
         CK(cudaMemsetAsync(h->tunebuf.p, 0, 3 * nx * sizeof(double), h->stream));
@@ -1151,9 +1189,29 @@ spmps_status do_apply(spmps_t* h, int k, const double* x, double* y, double* z, 
     S.p[8] = h->work3.as<double>();
     S.p[9] = h->work3.as<double>() + static_cast<int64_t>(h->G) * P->reduce_nx;
     const int G = h->G;
-    if (y && z) s = plan_run(h, *P, S, 0, 2 * G, st, ev);
-    else if (y) s = plan_run(h, *P, S, 0, G, st, ev);
-    else if (z) s = plan_run(h, *P, S, G, 2 * G, st, ev);
+    SlotsF SF{};
+    const SlotsF* split = nullptr;
+    if (h->apply_precision > 0 && y) {
+        // pre-split TF32 operands: environments once per update, x and T3 per action (plan_run)
+        for (EnvStore* E : {&h->Lenv[k], &h->Renv[k + 2]}) {
+            if (E->split_version != E->version) {
+                CK(E->split.ensure(std::max<int64_t>(1, E->total) * sizeof(float2)));
+                CK(launch_split_tf32(E->buf.as<double>(), E->total, static_cast<float2*>(E->split.p), st));
+                ++h->launches;
+                E->split_version = E->version;
+            }
+        }
+        CK(h->xsplit.ensure(std::max<int64_t>(1, P->reduce_nx) * sizeof(float2)));
+        CK(h->t3split.ensure(std::max<int64_t>(1, P->t2_size) * sizeof(float2)));
+        SF.p[0] = static_cast<float2*>(h->xsplit.p);
+        SF.p[4] = static_cast<float2*>(h->t3split.p);
+        SF.p[5] = static_cast<float2*>(h->Lenv[k].split.p);
+        SF.p[6] = static_cast<float2*>(h->Renv[k + 2].split.p);
+        split = &SF;
+    }
+    if (y && z) s = plan_run(h, *P, S, 0, 2 * G, st, ev, split);
+    else if (y) s = plan_run(h, *P, S, 0, G, st, ev, split);
+    else if (z) s = plan_run(h, *P, S, G, 2 * G, st, ev, split);
     if (s != SPMPS_OK) return s;
     ++h->applies;
     h->last_apply_flops = P->flops;
@@ -1278,7 +1336,7 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "jacobi_smem_max must be in [0, 112]");
     if (o.jacobi_smem_max == 0) o.jacobi_smem_max = 112;
-    if (o.precond < 0 || o.precond > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precond must be 0, 1 or 2");
+    if (o.precond < 0 || o.precond > 3) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precond must be 0, 1, 2 or 3");
     if (o.precision < 0 || o.precision > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precision must be 0, 1 or 2");
     if (o.autotune != 0 && o.autotune != 1) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "autotune must be 0 or 1");
     int ndev = 0;
@@ -1617,7 +1675,9 @@ spmps_status spmps_apply_heff_timed(spmps_handle h, int site, const double* x, d
     CK(cudaStreamSynchronize(h->stream));
     cudaEvent_t ev[5];
     for (auto& e : ev) CK(cudaEventCreate(&e));
+    h->apply_precision = h->opt.precision;
     st = do_apply(h, site, x, y, z, s, ev);
+    h->apply_precision = 0;
     if (st == SPMPS_OK) {
         CK(cudaEventSynchronize(ev[4]));
         for (int i = 0; i < 4; ++i) {

@@ -68,6 +68,9 @@ struct EnvStore {
     std::vector<int64_t> base;     // [op * G + g]
     int64_t total = 0;
     bool valid = false;
+    uint64_t version = 0;          // changes whenever buf is rewritten
+    DevMem split;                  // pre-split TF32 copy (float2 per element) for the tensor-core action
+    uint64_t split_version = 0;    // version of buf that split was made from (0: none)
 };
 
 // A three-phase contraction plan (GEMM, MPO-leg combination, GEMM), uploaded to the device.
@@ -76,6 +79,10 @@ struct Plan {
     CombPlan B;
     TilePolicy polA, polC;  // tile policies of phases A and C (autotuned per site, or the default)
     std::vector<int> tileA_rng, tileC_rng, combB_rng;  // [op * G + g] .. [op * G + g + 1]
+    // the builders write task ranges into tileA_rng / tileC_rng; the first upload keeps them here
+    // and every upload turns them into tile ranges for the tiles of its policy
+    std::vector<int> taskA_rng, taskC_rng;
+    bool task_rng_kept = false;
     std::vector<double> flopsA_rng, flopsB_rng, flopsC_rng;  // algorithmic flops per range
     int64_t t1_size = 0, t2_size = 0;
     int64_t reduce_nx = 0;  // > 0: phase C writes per-beta partials of this length (slots 8, 9)
@@ -120,6 +127,8 @@ struct spmps_t {
     // autotuner: chosen tile candidate per site for phases A and C (-1 = not tuned yet)
     std::vector<int> tune_a, tune_c;
     spmps::DevMem tunebuf;
+    uint64_t env_counter = 0;      // source of EnvStore versions
+    spmps::DevMem xsplit, t3split; // pre-split TF32 copies of x and of the phase-B output
     spmps::OpSet ops;        // H, N
     std::vector<spmps::Bond> bonds;           // K+1
     std::vector<spmps::RowBlockLayout> alay;  // per site, ns = 4
@@ -162,7 +171,8 @@ cudaError_t upload(DevMem& m, const std::vector<T>& v, cudaStream_t st) {
 bool validate_plan(const Plan& P, const int64_t* sizes, std::string* why);
 bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why);
 spmps_status plan_upload(spmps_t* h, Plan& P);
-spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t st, cudaEvent_t* ev = nullptr);
+spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                      const SlotsF* split = nullptr);
 spmps_status update_left(spmps_t* h, int i);
 spmps_status update_right(spmps_t* h, int i);
 spmps_status ensure_envs(spmps_t* h, int k);

@@ -6,6 +6,7 @@
 // tile of any task, every task of every beta point in the same launch.
 #include <cfloat>
 #include <cmath>
+#include <cooperative_groups.h>
 
 #include "kernels.h"
 
@@ -326,6 +327,20 @@ __global__ void __launch_bounds__(256) k_residual_diag(const double* __restrict_
         double den = dh[i] - theta * dn[i];
         if (fabs(den) < clamp) den = den < 0.0 ? -clamp : clamp;
         t[i] = -ri / den;
+    }
+}
+
+// out = v / (diag H - theta diag N), the denominator clamped as in k_residual_diag
+__global__ void __launch_bounds__(256) k_precond_apply(const double* __restrict__ v, const double* __restrict__ dh,
+                                                       const double* __restrict__ dn,
+                                                       const double* __restrict__ scal, double clamp, int64_t n,
+                                                       double* __restrict__ out) {
+    const double theta = scal[0];
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double den = dh[i] - theta * dn[i];
+        if (fabs(den) < clamp) den = den < 0.0 ? -clamp : clamp;
+        out[i] = v[i] / den;
     }
 }
 
@@ -712,19 +727,24 @@ __global__ void k_restart_coef(const double* __restrict__ cn, const double* __re
 
 // ---- batched Jacobi for the decimation --------------------------------------------------------
 constexpr int kJacobiSmemMax = 112;
+// cluster Jacobi: kJcC CTAs per matrix for dimensions in (kJcMin, kJcMax]
+constexpr int kJcC = 8;
+constexpr int kJcMin = 64;
+constexpr int kJcMax = 256;
 
 __global__ void __launch_bounds__(512) k_jacobi_batched(double* __restrict__ mats, double* __restrict__ vscratch,
                                                         double* __restrict__ evals,
                                                         const int64_t* __restrict__ mat_off,
                                                         const int64_t* __restrict__ val_off,
                                                         const int* __restrict__ dims, int smem_dim,
-                                                        int* __restrict__ status) {
+                                                        int skip_cluster, int* __restrict__ status) {
     extern __shared__ double smem[];
     __shared__ double cs_sh[2 * 256 + 4], red_sh[40], dg[512];
     __shared__ int pq_sh[2 * 256 + 4];
     const int b = blockIdx.x;
     const int n = dims[b];
     if (n <= 0) return;
+    if (skip_cluster && n > kJcMin && n <= kJcMax) return;  // handled by k_jacobi_cluster
     double* M = mats + mat_off[b];
     double *A, *V;
     if (n <= smem_dim) {  // the launch sized the dynamic shared memory for smem_dim
@@ -752,6 +772,165 @@ __global__ void __launch_bounds__(512) k_jacobi_batched(double* __restrict__ mat
         ev[rank] = vi;
         for (int r = 0; r < n; ++r) M[r * n + rank] = V[r * n + i];
     }
+}
+
+// ---- cluster Jacobi for the larger decimation blocks ------------------------------------------
+// One thread-block cluster of kJcC CTAs per density matrix of dimension in (kJcMin, kJcMax]: row r
+// of A and row r of V^T live in the shared memory of CTA r % kJcC.  The sweeps use the same
+// round-robin pairs, rotation formula, skip rule and stopping rule as jacobi_cta, so every element
+// receives the same rotations in the same order; each round is
+//   params of the CTA's pairs (from rows p and q, possibly remote) -> cluster barrier ->
+//   column update of the CTA's own rows (all pairs, local) -> cluster barrier ->
+//   row update of rows p, q of A and V^T for the CTA's pairs (distributed shared memory) ->
+//   cluster barrier.
+// The barriers are hardware cluster barriers that every CTA of the cluster executes the same
+// number of times (the stopping decision is made from the same partial sums on every CTA).
+namespace cgx = cooperative_groups;
+
+__global__ void __cluster_dims__(kJcC, 1, 1) __launch_bounds__(256)
+    k_jacobi_cluster(double* __restrict__ mats, double* __restrict__ evals, const int64_t* __restrict__ mat_off,
+                     const int64_t* __restrict__ val_off, const int* __restrict__ dims, int* __restrict__ status) {
+    extern __shared__ double jc_smem[];
+    __shared__ double cs_loc[2 * (kJcMax / 2) + 2];
+    __shared__ int pq_loc[2 * (kJcMax / 2) + 2];
+    __shared__ double part[2], red_sh[40];
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int rank = static_cast<int>(cl.block_rank());
+    const int b = blockIdx.x / kJcC;
+    const int n = dims[b];
+    if (n <= kJcMin || n > kJcMax) return;  // uniform over the cluster
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rows = (n - rank + kJcC - 1) / kJcC;  // rows r = rank + kJcC * i
+    const int rmax = (n + kJcC - 1) / kJcC;
+    double* Ar = jc_smem;                 // [rmax][n]
+    double* Vt = jc_smem + rmax * n;      // [rmax][n]
+    double* cs_own = Vt + rmax * n;       // params of this CTA's pairs, read by the others
+    int* pq_own = reinterpret_cast<int*>(cs_own + 2 * (kJcMax / 2) + 2);
+    double* M = mats + mat_off[b];
+    for (int e = tid; e < rows * n; e += nt) {
+        const int i = e / n, j = e - i * n;
+        const int r = rank + kJcC * i;
+        Ar[i * n + j] = M[static_cast<int64_t>(r) * n + j];
+        Vt[i * n + j] = r == j ? 1.0 : 0.0;
+    }
+    cl.sync();
+    auto row_ptr = [&](double* base, int r) -> double* {
+        double* local = base + (r / kJcC) * n;
+        return cl.map_shared_rank(local, r % kJcC);
+    };
+    const int np = (n + 1) & ~1, half = np / 2;
+    double off_prev = INFINITY;
+    int sweep = 0;
+    for (; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < rows * n; e += nt) {
+            const int i = e / n, j = e - i * n;
+            const int r = rank + kJcC * i;
+            const double v = Ar[i * n + j];
+            tot += v * v;
+            if (r != j) off += v * v;
+        }
+        off = block_sum(off, red_sh);
+        if (tid == 0) part[0] = off;
+        tot = block_sum(tot, red_sh);
+        if (tid == 0) part[1] = tot;
+        cl.sync();
+        off = 0.0;
+        tot = 0.0;
+        for (int c = 0; c < kJcC; ++c) {  // same order on every CTA
+            const double* pr = cl.map_shared_rank(part, c);
+            off += pr[0];
+            tot += pr[1];
+        }
+        cl.sync();  // the partials are read before they are overwritten
+        if (off <= 1e-28 * tot || off == 0.0 || (off <= 1e-20 * tot && off > 0.25 * off_prev)) break;
+        off_prev = off;
+        const double tiny = 1e-18 * sqrt(tot);
+        for (int round = 0; round < np - 1; ++round) {
+            // rotation parameters of the pairs i = rank, rank + kJcC, ...
+            for (int i = rank + kJcC * tid; i < half; i += kJcC * nt) {
+                auto player = [&](int k) { return k == 0 ? 0 : 1 + ((k - 1 + round) % (np - 1)); };
+                int p = player(i), q = player(np - 1 - i);
+                if (p > q) { const int t = p; p = q; q = t; }
+                double c = 1.0, sn = 0.0;
+                if (q < n) {
+                    const double apq = row_ptr(Ar, p)[q];
+                    if (fabs(apq) > tiny) {
+                        const double app = row_ptr(Ar, p)[p], aqq = row_ptr(Ar, q)[q];
+                        const double theta = (aqq - app) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sn = t * c;
+                    } else {
+                        q = -1;
+                    }
+                } else {
+                    q = -1;
+                }
+                pq_own[2 * i] = p;
+                pq_own[2 * i + 1] = q;
+                cs_own[2 * i] = c;
+                cs_own[2 * i + 1] = sn;
+            }
+            cl.sync();
+            for (int i = tid; i < half; i += nt) {
+                const int src = i % kJcC;
+                const int* pqr = cl.map_shared_rank(pq_own, src);
+                const double* csr = cl.map_shared_rank(cs_own, src);
+                pq_loc[2 * i] = pqr[2 * i];
+                pq_loc[2 * i + 1] = pqr[2 * i + 1];
+                cs_loc[2 * i] = csr[2 * i];
+                cs_loc[2 * i + 1] = csr[2 * i + 1];
+            }
+            __syncthreads();
+            // columns p, q of the own rows
+            for (int e = tid; e < rows * half; e += nt) {
+                const int i = e / half, pi = e - i * half;
+                const int p = pq_loc[2 * pi], q = pq_loc[2 * pi + 1];
+                if (q < 0) continue;
+                const double c = cs_loc[2 * pi], sn = cs_loc[2 * pi + 1];
+                const double ap = Ar[i * n + p], aq = Ar[i * n + q];
+                Ar[i * n + p] = c * ap - sn * aq;
+                Ar[i * n + q] = sn * ap + c * aq;
+            }
+            cl.sync();
+            // rows p, q of A and of V^T for this CTA's pairs
+            for (int i = rank; i < half; i += kJcC) {
+                const int p = pq_loc[2 * i], q = pq_loc[2 * i + 1];
+                if (q < 0) continue;
+                const double c = cs_loc[2 * i], sn = cs_loc[2 * i + 1];
+                double* ap = row_ptr(Ar, p);
+                double* aq = row_ptr(Ar, q);
+                double* vp = row_ptr(Vt, p);
+                double* vq = row_ptr(Vt, q);
+                for (int j = tid; j < n; j += nt) {
+                    const double x = ap[j], y = aq[j];
+                    ap[j] = c * x - sn * y;
+                    aq[j] = sn * x + c * y;
+                    const double u = vp[j], w = vq[j];
+                    vp[j] = c * u - sn * w;
+                    vq[j] = sn * u + c * w;
+                }
+            }
+            cl.sync();
+        }
+    }
+    if (tid == 0 && rank == 0 && sweep >= 60) atomicExch(status, 1);
+    // eigenpairs sorted by descending eigenvalue (rank sort, ties by index): the CTA writes the
+    // eigenvalues and eigenvector columns of its own rows
+    double* ev = evals + val_off[b];
+    for (int i = tid; i < rows; i += nt) {
+        const int r = rank + kJcC * i;
+        const double vi = Ar[i * n + r];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const double vj = row_ptr(Ar, j)[j];
+            if (vj > vi || (vj == vi && j < r)) ++rk;
+        }
+        ev[rk] = vi;
+        for (int q = 0; q < n; ++q) M[static_cast<int64_t>(q) * n + rk] = Vt[i * n + q];
+    }
+    cl.sync();  // no CTA leaves while others still read its shared memory
 }
 
 // ---- ordered truncation (one CTA) ---------------------------------------------------------------
@@ -952,6 +1131,12 @@ cudaError_t launch_residual_diag(const double* hx, const double* nx, const doubl
     return launch_norm2(r, n, red, partial, st);
 }
 
+cudaError_t launch_precond_apply(const double* v, const double* dh, const double* dn, const double* scal,
+                                 double clamp, int64_t n, double* out, cudaStream_t st) {
+    k_precond_apply<<<grid_for(n, 256, 2048), 256, 0, st>>>(v, dh, dn, scal, clamp, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_norm2(const double* x, int64_t n, double* out, double* partial, cudaStream_t st) {
     const int nb = grid_for(n, 256, kRedBlocks);
     k_norm2_partial<<<nb, 256, 0, st>>>(x, n, partial);
@@ -985,7 +1170,7 @@ cudaError_t launch_restart_coef(const double* c_new, const double* c_old, int m,
 
 cudaError_t launch_jacobi_batched(double* mats, double* vscratch, double* evals, const int64_t* mat_off,
                                   const int64_t* val_off, const int* dims, int n_mats, int max_dim, int smem_limit,
-                                  int* status, cudaStream_t st) {
+                                  int cluster, int* status, cudaStream_t st) {
     if (n_mats <= 0) return cudaSuccess;
     if (max_dim > 512) return cudaErrorInvalidValue;  // pair tables hold at most 256 pairs
     // matrices up to sm_dim run in shared memory (A and V), larger ones in global memory
@@ -995,7 +1180,21 @@ cudaError_t launch_jacobi_batched(double* mats, double* vscratch, double* evals,
     cudaError_t e = cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          2 * kJacobiSmemMax * kJacobiSmemMax * static_cast<int>(sizeof(double)));
     if (e != cudaSuccess) return e;
-    k_jacobi_batched<<<n_mats, 512, smem, st>>>(mats, vscratch, evals, mat_off, val_off, dims, sm_dim, status);
+    const bool use_cluster = cluster && max_dim > kJcMin;
+    if (use_cluster) {
+        // rows of A and V^T per CTA, plus the pair table of the CTA
+        const int dmax = max_dim < kJcMax ? max_dim : kJcMax;
+        const int rmax = (dmax + kJcC - 1) / kJcC;
+        const size_t csm = (static_cast<size_t>(2) * rmax * dmax + 2 * (kJcMax / 2) + 2) * sizeof(double) +
+                           (2 * (kJcMax / 2) + 2) * sizeof(int);
+        e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(csm));
+        if (e != cudaSuccess) return e;
+        k_jacobi_cluster<<<n_mats * kJcC, 256, csm, st>>>(mats, evals, mat_off, val_off, dims, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_jacobi_batched<<<n_mats, 512, smem, st>>>(mats, vscratch, evals, mat_off, val_off, dims, sm_dim,
+                                                use_cluster ? 1 : 0, status);
     return cudaGetLastError();
 }
 

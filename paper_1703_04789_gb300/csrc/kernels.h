@@ -20,6 +20,18 @@ cudaError_t launch_sum_partials(const double* partial, int G, int64_t n, double*
 cudaError_t launch_gemm_tf32(const Slots& slots, const GemmTask* tasks, const GemmSeg* segs, const GemmTile* tiles,
                              const int* cmaps, int n_tiles, int split3, cudaStream_t st);
 
+// Operand buffers in pre-split TF32 form (float2 = (hi, lo) per element), indexed by the same slot
+// handles as the FP64 buffers.
+struct SlotsF {
+    float2* p[kMaxSlots];
+};
+// out[i] = (tf32(float(x[i])), tf32(float(x[i]) - hi)).
+cudaError_t launch_split_tf32(const double* x, int64_t n, float2* out, cudaStream_t st);
+// The TF32 / 3xTF32 task lists with every A and B operand read from the pre-split buffers of the
+// same slots (no conversion in the GEMM); C written in FP64 as launch_gemm_tf32.
+cudaError_t launch_gemm_tf32s(const Slots& slots, const SlotsF& split, const GemmTask* tasks, const GemmSeg* segs,
+                              const GemmTile* tiles, const int* cmaps, int n_tiles, int split3, cudaStream_t st);
+
 // Linear combination of equally shaped blocks (the MPO-leg contraction).
 cudaError_t launch_comb_f64(const Slots& slots, const CombOut* outs, const CombTerm* terms, int n_outs,
                             cudaStream_t st);
@@ -69,6 +81,9 @@ cudaError_t launch_norm2(const double* x, int64_t n, double* out, double* partia
 // x *= 1/sqrt(*nrm2) (device scalar)
 cudaError_t launch_scale_inv_sqrt(double* x, int64_t n, const double* nrm2, cudaStream_t st);
 // x += alpha * y, alpha = sign * num / den from device scalars (for CG)
+// out = v / (diag H - theta diag N) (denominator clamped to |.| >= clamp; theta = scal[0])
+cudaError_t launch_precond_apply(const double* v, const double* dh, const double* dn, const double* scal,
+                                 double clamp, int64_t n, double* out, cudaStream_t st);
 cudaError_t launch_axpy_ratio(double* x, const double* y, int64_t n, const double* num, const double* den,
                               double sign, cudaStream_t st);
 // p = r + (num/den) p
@@ -85,10 +100,12 @@ cudaError_t launch_restart_coef(const double* c_new, const double* c_old, int m,
 // mats: concatenated row-major n_i x n_i matrices (overwritten by the eigenvector matrices,
 // columns = vectors, sorted by descending eigenvalue), evals: concatenated eigenvalues.
 // vscratch: same size as mats (used for matrices above the shared-memory limit of 112).
-// Matrices up to min(smem_limit, 112) run in shared memory.
+// Matrices up to min(smem_limit, 112) run in shared memory.  With cluster != 0, matrices of
+// dimension 65..256 run on a thread-block cluster of 8 CTAs each (rows distributed over the
+// CTAs' shared memory), the others on one CTA.
 cudaError_t launch_jacobi_batched(double* mats, double* vscratch, double* evals, const int64_t* mat_off,
                                   const int64_t* val_off, const int* dims, int n_mats, int max_dim, int smem_limit,
-                                  int* status, cudaStream_t st);
+                                  int cluster, int* status, cudaStream_t st);
 
 // Ordered truncation of singular values sqrt(max(evals, 0)) (one CTA): values within
 // tie_rtol * max of their sorted predecessor form a cluster ordered by (n, 2m, index);

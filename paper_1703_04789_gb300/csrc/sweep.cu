@@ -231,7 +231,11 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
     out->converged = false;
     for (int it = 1; it <= cap; ++it) {
         int rec = h->profile ? prof_begin(h, h->stream, 2, 0.0) : -1;
-        CK(launch_ritz_inc(B.hm.as<double>(), B.nm.as<double>(), ms, m, reset, kEpsMetric, B.ritz.as<RitzState>(),
+        // with a reduced-precision H the relation ker N_eff in ker H_eff holds only to that precision:
+        // directions of small N-norm would carry spurious Ritz values of order eps |H| / nu, so the
+        // metric range kept before the switch to FP64 is cut well above that error
+        const double eps_metric = switched ? kEpsMetric : (h->apply_precision == 1 ? 1e-2 : 1e-6);
+        CK(launch_ritz_inc(B.hm.as<double>(), B.nm.as<double>(), ms, m, reset, eps_metric, B.ritz.as<RitzState>(),
                            B.coef.as<double>(), sc, h->stream));
         if (rec >= 0) prof_end(h, h->stream, rec);
         reset = 0;
@@ -246,6 +250,16 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         if (h->opt.precond == 1) {
             st = metric_cg(h, k, B, n, B.r.as<double>(), B.t.as<double>());
             if (st != SPMPS_OK) return st;
+        } else if (h->opt.precond == 3) {
+            // Olsen: t = M^-1 (-r + eps N x), eps such that x^T N t = 0, M = diag H - theta diag N:
+            // t = t_diag + eps u, u = M^-1 N x, eps = -(Nx . t_diag) / (Nx . u)
+            CK(launch_precond_apply(B.nx.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, kClamp, n,
+                                    B.cg_ap.as<double>(), h->stream));
+            CK(launch_multidot(B.nx.as<double>(), 0, 1, B.t.as<double>(), n, sc + 11, h->partial.as<double>(), h->stream));
+            CK(launch_multidot(B.nx.as<double>(), 0, 1, B.cg_ap.as<double>(), n, sc + 12, h->partial.as<double>(),
+                               h->stream));
+            CK(launch_axpy_ratio(B.t.as<double>(), B.cg_ap.as<double>(), n, sc + 11, sc + 12, -1.0, h->stream));
+            h->launches += 6;
         }
         if (harvest || learned) {
             // |d|^2 of the diagonal correction (sc[7]) for the features
@@ -330,7 +344,11 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
             best_rn = rn;
             best_it = it;
         }
-        if (!switched && (rn < switch_tol || it - best_it >= kStagnation)) {
+        // plain TF32 (precision 1) has a noise floor near its switch tolerance: switch on stagnation
+        // too; 3xTF32 reaches its tolerance well above its floor
+        const bool stagnated = h->apply_precision == 1 && it - best_it >= kStagnation;
+        // and every solve finishes in FP64: switch at half the iteration cap at the latest
+        if (!switched && (rn < switch_tol || stagnated || it >= cap / 2)) {
             // the new direction (column m) is applied in FP64 below
             st = switch_to_fp64(it);
             if (st != SPMPS_OK) return st;
@@ -563,7 +581,7 @@ spmps_status decimate(spmps_t* h, int k, double* x, int Dmax, bool move_right, D
     CK(cudaMemsetAsync(B.status.p, 0, sizeof(int), h->stream));
     const int rec_eig = h->profile ? prof_begin(h, h->stream, 4, 0.0) : -1;
     CK(launch_jacobi_batched(B.mats.as<double>(), B.vscr.as<double>(), B.evals.as<double>(), B.mat_off.as<int64_t>(),
-                             B.val_off.as<int64_t>(), B.dims.as<int>(), nm, maxdim, h->opt.jacobi_smem_max,
+                             B.val_off.as<int64_t>(), B.dims.as<int>(), nm, maxdim, h->opt.jacobi_smem_max, 1,
                              B.status.as<int>(), h->stream));
     CK(launch_truncate(B.evals.as<double>(), B.val_off.as<int64_t>(), B.dims.as<int>(), B.ln.as<int>(), B.ltm.as<int>(),
                        nm, total, Dmax, kTieRtol, kDropAbs, B.keep.as<int>(), B.keep_total.as<int>(), B.disc.as<double>(),

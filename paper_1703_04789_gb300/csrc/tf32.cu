@@ -144,6 +144,118 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(Slots S, const GemmTask* __re
         }
 }
 
+// ---- pre-split operands -----------------------------------------------------------------------
+// The conversion FP64 -> FP32 -> (hi, lo) runs once per operand buffer (environment after its
+// update, x and the phase-B output once per action) instead of once per fragment load: on this
+// part the FP64 conversions run at the FP64 rate, so converting inside the GEMM made it as slow
+// as the FP64 kernel.  hi = tf32(float(v)), lo = tf32(float(v) - hi), stored as one float2.
+__global__ void __launch_bounds__(256) k_split_tf32(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint32_t hi, lo;
+        split(x[i], hi, lo);
+        out[i] = make_float2(__uint_as_float(hi), __uint_as_float(lo));
+    }
+}
+
+__device__ __forceinline__ const float2* resolve_s(const SlotsF& F, uint64_t h) {
+    return F.p[h >> 56] + static_cast<int64_t>(h & 0x00FFFFFFFFFFFFFFull);
+}
+
+template <bool SPLIT3>
+__global__ void __launch_bounds__(128) k_gemm_tf32s(Slots S, SlotsF F, const GemmTask* __restrict__ tasks,
+                                                    const GemmSeg* __restrict__ segs, const GemmTile* __restrict__ tiles,
+                                                    const int* __restrict__ cmaps, int n_tiles) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_tiles) return;
+    const GemmTile tl = tiles[warp];
+    const GemmTask T = tasks[tl.task];
+    int rh, rw;
+    region(tl, rh, rw);
+    const int rmax = min(T.M, tl.m0 + rh), cmax = min(T.N, tl.n0 + rw);
+    const int g = lane >> 2, q = lane & 3;
+    double* C = resolve_t(S, T.c);
+    const int* cm = T.cmap >= 0 ? cmaps + T.cmap : nullptr;
+    const float2 zero = make_float2(0.0f, 0.0f);
+    for (int sm0 = tl.m0; sm0 < rmax; sm0 += 32)
+        for (int sn0 = tl.n0; sn0 < cmax; sn0 += 32) {
+            float acc[2][4][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+            const int mt = (min(32, rmax - sm0) + 15) / 16;
+            const int nt = (min(32, cmax - sn0) + 7) / 8;
+            for (int sgi = 0; sgi < T.nseg; ++sgi) {
+                const GemmSeg sg = segs[T.seg0 + sgi];
+                const float2* __restrict__ A = resolve_s(F, sg.a);
+                const float2* __restrict__ B = resolve_s(F, sg.b);
+                for (int k0 = 0; k0 < sg.K; k0 += 8) {
+                    uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int r = sm0 + 16 * i + g + ((e & 1) ? 8 : 0);
+                            const int k = k0 + q + ((e & 2) ? 4 : 0);
+                            const float2 v = (i < mt && r < rmax && k < sg.K)
+                                                 ? A[static_cast<int64_t>(r) * sg.a_rs + static_cast<int64_t>(k) * sg.a_cs]
+                                                 : zero;
+                            ah[i][e] = __float_as_uint(v.x);
+                            al[i][e] = __float_as_uint(v.y);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int k = k0 + q + (e ? 4 : 0);
+                            const int c = sn0 + 8 * j + g;
+                            const float2 v = (j < nt && c < cmax && k < sg.K)
+                                                 ? B[static_cast<int64_t>(k) * sg.b_rs + static_cast<int64_t>(c) * sg.b_cs]
+                                                 : zero;
+                            bh[j][e] = __float_as_uint(v.x);
+                            bl[j][e] = __float_as_uint(v.y);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        if (i >= mt) continue;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if (j >= nt) continue;
+                            mma_tf32(acc[i][j], ah[i], bh[j]);
+                            if (SPLIT3) {
+                                mma_tf32(acc[i][j], ah[i], bl[j]);
+                                mma_tf32(acc[i][j], al[i], bh[j]);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i >= mt) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j >= nt) continue;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int r = sm0 + 16 * i + g + ((e & 2) ? 8 : 0);
+                        const int c = sn0 + 8 * j + 2 * q + (e & 1);
+                        if (r < rmax && c < cmax) {
+                            const int64_t cc = cm ? cm[c] : c;
+                            C[static_cast<int64_t>(r) * T.ldc + cc] = static_cast<double>(acc[i][j][e]);
+                        }
+                    }
+                }
+            }
+        }
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_tf32(const Slots& slots, const GemmTask* tasks, const GemmSeg* segs, const GemmTile* tiles,
@@ -154,6 +266,26 @@ cudaError_t launch_gemm_tf32(const Slots& slots, const GemmTask* tasks, const Ge
         k_gemm_tf32<true><<<grid, 128, 0, st>>>(slots, tasks, segs, tiles, cmaps, n_tiles);
     else
         k_gemm_tf32<false><<<grid, 128, 0, st>>>(slots, tasks, segs, tiles, cmaps, n_tiles);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_split_tf32(const double* x, int64_t n, float2* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_split_tf32<<<static_cast<int>(blocks), 256, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tf32s(const Slots& slots, const SlotsF& split, const GemmTask* tasks, const GemmSeg* segs,
+                              const GemmTile* tiles, const int* cmaps, int n_tiles, int split3, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const int grid = (n_tiles + 3) / 4;
+    if (split3)
+        k_gemm_tf32s<true><<<grid, 128, 0, st>>>(slots, split, tasks, segs, tiles, cmaps, n_tiles);
+    else
+        k_gemm_tf32s<false><<<grid, 128, 0, st>>>(slots, split, tasks, segs, tiles, cmaps, n_tiles);
     return cudaGetLastError();
 }
 

@@ -154,3 +154,26 @@ def test_planner_flop_count_matches_independent_count():
         ref = bench._count_apply_flops(inputs.mps_structure(L, N, 0, D), k, M.hubbard_mpo(L, 1.0, 4.0), G, 0, 0)
         assert abs(lib - ref) <= 1e-9 * ref, (k, lib, ref)
     dev.close()
+
+
+@pytest.mark.gpu
+def test_autotuned_tiles_give_the_same_action():
+    """The autotuner only changes tile shapes (summation order): the action agrees with the
+    default tiling to rounding, at every site."""
+    require_gpu()
+    case = (8, 8, 0, 0, 32, 5, 1, 4.0)
+    from paper_1703_04789_gb300 import Spmps
+    L, N, twoM, twoS, D, G, seed, U = case
+    P, dev = _setup(*case)
+    tuned = Spmps(L, N, twoM, twoS, G, D, autotune=True)
+    tuned.set_hubbard(1.0, U)
+    tuned.set_mps(P.mps.labels, P.mps.A, center=0)
+    rng = np.random.default_rng(7)
+    for k in range(L - 1):
+        xv = rng.standard_normal(dev.x_layout(k)["n_x"])
+        y0, z0 = dev.apply_heff_host(k, xv)
+        y1, z1 = tuned.apply_heff_host(k, xv)
+        assert np.abs(y1 - y0).max() <= 1e-12 * max(1.0, np.abs(y0).max())
+        assert np.abs(z1 - z0).max() <= 1e-12 * max(1.0, np.abs(z0).max())
+    dev.close()
+    tuned.close()

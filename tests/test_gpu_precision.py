@@ -59,3 +59,29 @@ def test_refined_theta_matches_fp64(prec):
         out[p] = d.optimize_step(0, True)
         d.close()
     assert abs(out[prec][0] - out["fp64"][0]) < 1e-9 * max(1.0, abs(out["fp64"][0])), out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
+def test_mixed_precision_sweeps_match_fp64(prec):
+    """Whole sweeps with the reduced-precision action in the first Davidson stage (autotuned
+    tiles, pre-split tensor-core operands, environments updated along the way): at D above the
+    exact Schmidt rank both forms reach the same exact singlet energy, and every solve finishes
+    in FP64."""
+    require_gpu()
+    from paper_1703_04789_gb300 import Spmps
+    L, N, D, G = 8, 8, 256, 5
+    labels, tens = inputs.random_mps(L, N, 0, D, 4)
+    out = {}
+    for p in ("fp64", prec):
+        dev = Spmps(L, N, 0, 0, G, D, precision=p, autotune=True)
+        dev.set_hubbard(1.0, 4.0)
+        dev.set_mps(labels, tens, center=0)
+        dev.canonicalize()
+        E, _ = dev.sweep(3)
+        out[p] = E
+        if p != "fp64":
+            it, refine = dev.davidson_stats()
+            assert refine > 0
+        dev.close()
+    assert abs(out[prec][-1] - out["fp64"][-1]) < 1e-8, (out[prec], out["fp64"])

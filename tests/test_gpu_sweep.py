@@ -140,6 +140,26 @@ def test_metric_cg_preconditioner_converges_to_the_same_theta():
 
 
 @pytest.mark.gpu
+def test_olsen_correction_converges_to_the_same_theta():
+    """precond = olsen (diagonal correction made N-orthogonal to x): the solve converges to the
+    oracle's lowest generalised eigenvalue, the same as with the diagonal correction."""
+    require_gpu()
+    L, N, twoM, twoS, D, G = 6, 6, 0, 0, 12, 4
+    labels, tens = inputs.random_mps(L, N, twoM, D, 3)
+    P = S.prepare(labels, tens, M.hubbard_mpo(L, 1.0, 4.0), twoS, twoM, G)
+    dev = _dev(L, N, twoM, twoS, D, G, precond="olsen", dav_tol_r=1e-9, dav_max_iter=400)
+    dev.set_mps(P.mps.labels, P.mps.A, center=0)
+    th, it = dev.optimize_step(0, True)
+    x0 = P.two_site(0)
+    mask = S.two_site_mask(P.mps.labels[0], P.mps.labels[2])
+    dh, dn = P.diagonal(0)
+    res = S.davidson(lambda v: P.apply(v, 0), x0, dh, dn, mask, tol_r=1e-9, max_iter=400)
+    assert res.converged
+    assert abs(th - res.theta) < 1e-9 * max(1.0, abs(res.theta))
+    dev.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("smem_max", [0, 8])
 def test_eight_site_untruncated_sweeps_reach_ed(smem_max):
     """L=8 half filling, D=256 (no truncation: the exact middle-bond rank is 256), n_beta=5:
