@@ -4,7 +4,9 @@
 S=1) the way the benchmark does: seeded random MPS, GPU canonicalisation, warm-up sweeps,
 checkpoint.  ``python -m paper_1703_04789_gb300.workloads --sweeps W --applies A`` runs the
 warm-up sweeps and then A projected actions at the middle site of the optimised MPS, so that a
-profiler can capture the block-GEMM launches of a converged state.
+profiler can capture the block-GEMM launches of a converged state; with ``--profile-sweep`` it
+also runs one more full sweep of the S=0 target inside the NVTX range ``profile_sweep`` (the
+launches of every kernel kind of a sweep, for a launch list).
 """
 from __future__ import annotations
 
@@ -35,11 +37,13 @@ def main():
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--applies", type=int, default=3)
     ap.add_argument("--site", type=int, default=11)
+    ap.add_argument("--profile-sweep", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
     args = ap.parse_args()
     import torch
     from . import build
     build.build()
-    h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]])[0]
+    h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune)[0]
     dev = h["dev"]
     lay = dev.x_layout(args.site)
     x = torch.tensor(np.random.default_rng(0).standard_normal(lay["n_x"]), device="cuda")
@@ -54,6 +58,15 @@ def main():
     fl = dev.apply_flops(args.site)
     print({"n_x": lay["n_x"], "flops": fl.tolist(), "phase_ms": ms.tolist(),
            "gemm_tflops": float((fl[0] + fl[2]) / ((ms[1] + ms[3]) * 1e-3) / 1e12)})
+    if args.profile_sweep:
+        ck = dev.get_mps()
+        dev.set_mps(*ck[:2], center=ck[2])
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profile_sweep")
+        E, _ = dev.sweep(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print({"profile_sweep_E": float(E[0]), "iterations": dev.davidson_stats()[0]})
 
 
 if __name__ == "__main__":
