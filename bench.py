@@ -41,7 +41,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SP-MPS sweep time & projected H_eff·x TFLOP/s vs FP64 plain at 1e-6 Eh"
 # Projected actions per sweep of the FP64 plain form on this workload (measured on GB300, mean of
 # the two targets); scales the oracle's per-action time to a sweep for --impl reference.
-ACTIONS_PER_PLAIN_SWEEP = 5900
+ACTIONS_PER_PLAIN_SWEEP = 5745
+# DRAM bytes per k_gemm_f64 launch of the middle-site action (phase A 63.1 MB, phase C 113.5 MB,
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel)
+TRAFFIC_PER_LAUNCH = 88.3e6
 WORKLOAD = {
     "workload": "Hubbard chain L=24 open, t=1, U=4, N=24, targets (2M,2S)=(0,0) and (2,2), D=256, "
                 "n_beta=8; step = one two-site sweep per target from a checkpoint taken after the warm-up sweeps",
@@ -226,6 +229,17 @@ def run_ours(args):
         d.sweep(1)
     e2e_s = time.perf_counter() - t0
     e2e_value = len(hs) * world / e2e_s
+    # the dominant kernel at the middle site of the S=0 target: phases A and C of the action
+    # (k_gemm_f64), CUDA events on the handle's stream, warm
+    d0 = fast[0]
+    site = WORKLOAD["site"]
+    lay = d0.x_layout(site)
+    xs = torch.tensor(np.random.default_rng(0).standard_normal(lay["n_x"]), device="cuda")
+    ys, zs = torch.empty_like(xs), torch.empty_like(xs)
+    d0.apply_heff(site, xs, ys, zs)
+    torch.cuda.synchronize()
+    phase = np.mean([d0.apply_heff_timed(site, xs, ys, zs) for _ in range(5)], axis=0)
+    fl_site = d0.apply_flops(site)
     for d in fast:
         d.close()
 
@@ -271,13 +285,21 @@ def run_ours(args):
         "variants_2S=0": variants,
         "learned_correction": mlp_info,
         "apply_tflops": round(apply_flops / (total_ms * 1e-3) / 1e12, 6),
-        "roofline": {"bound": "alu", "kernel": "k_gemm_f64 (all block GEMMs of the timed sweeps)",
-                     "achieved": round(g_fl / (g_ms * 1e-3) / 1e12, 6) if g_ms > 0 else 0.0,
+        "roofline": {"bound": "alu",
+                     "kernel": "k_gemm_f64, phases A and C of the projected action at sites (11, 12), S=0",
+                     "achieved": round(float(fl_site[0] + fl_site[2]) / ((phase[1] + phase[3]) * 1e-3) / 1e12, 6),
                      "peak": round(peak, 6), "unit": "TFLOP/s",
-                     "frac": round(g_fl / (g_ms * 1e-3) / 1e12 / peak, 4) if g_ms > 0 and peak else None,
-                     "peak_source": "measured FP64 FMA-chain kernel on all SMs (nominal 1.25)",
-                     "traffic": None, "launches": g_n, "avg_launch_ms": round(g_ms / max(1, g_n), 5),
-                     "share_of_sweep": round(g_ms / total_ms, 4) if total_ms else None},
+                     "frac": round(float(fl_site[0] + fl_site[2]) / ((phase[1] + phase[3]) * 1e-3) / 1e12 / peak, 4)
+                     if peak else None,
+                     "peak_source": "measured FP64 FMA-chain kernel on all SMs (spmps_device_fp64_peak; nominal 1.25)",
+                     "traffic": TRAFFIC_PER_LAUNCH,
+                     "traffic_note": "bytes per launch (mean of the phase-A and phase-C launches), ncu capture in "
+                                     "profiles/k_gemm_f64_hubbard_L24_D256.md",
+                     "phase_ms": [round(float(v), 4) for v in phase],
+                     "sweep_gemms": {"achieved": round(g_fl / (g_ms * 1e-3) / 1e12, 6) if g_ms > 0 else 0.0,
+                                     "frac": round(g_fl / (g_ms * 1e-3) / 1e12 / peak, 4) if g_ms > 0 and peak else None,
+                                     "launches": g_n, "avg_launch_ms": round(g_ms / max(1, g_n), 5),
+                                     "share_of_sweep": round(g_ms / total_ms, 4) if total_ms else None}},
         "time_breakdown_ms": dict(breakdown, total_sweep_ms=round(total_ms, 2)),
         "e2e": {"value": round(e2e_value, 6), "unit": "sweeps/s", "h2d_bytes_per_step": sum(h["ckpt_bytes"] for h in hs),
                 "d2h_bytes_per_step": 8 * len(hs)},

@@ -182,7 +182,11 @@ struct GemmPlan {
     std::vector<int> cmaps;
     double flops = 0.0;
     void add_tiles(const TilePolicy& pol = TilePolicy());
-    void clear() { tasks.clear(); segs.clear(); tiles.clear(); cmaps.clear(); flops = 0.0; }
+    // tiles for the tensor-core kernel: regions of at most 32 x 32 outputs (one MMA sub-tile per
+    // warp), shape 6
+    std::vector<GemmTile> tc_tiles;
+    void add_tc_tiles();
+    void clear() { tasks.clear(); segs.clear(); tiles.clear(); tc_tiles.clear(); cmaps.clear(); flops = 0.0; }
 };
 struct CombPlan {
     std::vector<CombOut> outs;

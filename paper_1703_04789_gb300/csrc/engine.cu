@@ -146,9 +146,15 @@ bool validate_gemm(const GemmPlan& G, const int64_t* sizes, std::string* why) {
     return validate_tiles(G, why);
 }
 
+bool validate_tile_list(const GemmPlan& G, const std::vector<GemmTile>& tiles, std::string* why);
+
 bool validate_tiles(const GemmPlan& G, std::string* why) {
-    for (const GemmTile& t : G.tiles) {
-        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 5) {
+    return validate_tile_list(G, G.tiles, why) && validate_tile_list(G, G.tc_tiles, why);
+}
+
+bool validate_tile_list(const GemmPlan& G, const std::vector<GemmTile>& tiles, std::string* why) {
+    for (const GemmTile& t : tiles) {
+        if (t.task < 0 || t.task >= static_cast<int>(G.tasks.size()) || t.shape < 0 || t.shape > 6) {
             *why = "bad tile";
             return false;
         }
@@ -157,6 +163,10 @@ bool validate_tiles(const GemmPlan& G, std::string* why) {
         if (t.shape == 5 && (t.tm < 1 || t.tn < 1 || t.tm > 32 || t.tn > 32 || t.tm * t.tn > 256 ||
                              t.m0 + t.tm > T.M || t.n0 + t.tn > T.N)) {
             *why = "bad warp-block tile";
+            return false;
+        }
+        if (t.shape == 6 && (t.tm < 1 || t.tn < 1 || t.tm > 32 || t.tn > 32 || t.m0 + t.tm > T.M || t.n0 + t.tn > T.N)) {
+            *why = "bad tensor-core tile";
             return false;
         }
     }
@@ -198,6 +208,8 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
     } done{h, t0};
     P.A.add_tiles(P.polA);
     P.C.add_tiles(P.polC);
+    P.A.add_tc_tiles();
+    P.C.add_tc_tiles();
     {
         std::string why;
         if (!validate_tiles(P.A, &why) || !validate_tiles(P.C, &why)) return fail(h, SPMPS_ERR_CUDA, "internal tile check: " + why);
@@ -212,14 +224,16 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
     CK(upload(P.d_segsC, P.C.segs, h->stream));
     CK(upload(P.d_tilesC, P.C.tiles, h->stream));
     CK(upload(P.d_cmapsC, P.C.cmaps, h->stream));
+    CK(upload(P.d_tcA, P.A.tc_tiles, h->stream));
+    CK(upload(P.d_tcC, P.C.tc_tiles, h->stream));
     CK(upload(P.d_diag_blocks, P.diag_blocks, h->stream));
     CK(upload(P.d_diag_terms, P.diag_terms, h->stream));
     // tile and output ranges per (op, g): tasks were appended in (op, g) order
-    auto ranges = [&](const GemmPlan& gp, const std::vector<int>& task_rng, std::vector<int>& out) {
+    auto ranges = [&](const std::vector<GemmTile>& tiles, const std::vector<int>& task_rng, std::vector<int>& out) {
         out.assign(task_rng.size(), 0);
         size_t t = 0;
         for (size_t r = 0; r < task_rng.size(); ++r) {
-            while (t < gp.tiles.size() && gp.tiles[t].task < task_rng[r]) ++t;
+            while (t < tiles.size() && tiles[t].task < task_rng[r]) ++t;
             out[r] = static_cast<int>(t);
         }
     };
@@ -244,8 +258,10 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
     for (size_t r = 0; r + 1 < P.combB_rng.size(); ++r)
         for (int o = P.combB_rng[r]; o < P.combB_rng[r + 1]; ++o)
             P.flopsB_rng[r] += 2.0 * P.B.outs[o].rows * P.B.outs[o].cols * P.B.outs[o].nterm;
-    ranges(P.A, a_task_rng, P.tileA_rng);
-    ranges(P.C, c_task_rng, P.tileC_rng);
+    ranges(P.A.tiles, a_task_rng, P.tileA_rng);
+    ranges(P.C.tiles, c_task_rng, P.tileC_rng);
+    ranges(P.A.tc_tiles, a_task_rng, P.tcA_rng);
+    ranges(P.C.tc_tiles, c_task_rng, P.tcC_rng);
     CK(h->work1.ensure(std::max<int64_t>(1, P.t1_size) * sizeof(double)));
     CK(h->work2.ensure(std::max<int64_t>(1, P.t2_size) * sizeof(double)));
     CK(cudaStreamSynchronize(h->stream));
@@ -272,15 +288,17 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
     const int prec = P.reduce_nx > 0 ? h->apply_precision : 0;
     const int G = h->G;
     auto gemm = [&](const DevMem& tasks, const DevMem& segs, const DevMem& tiles, const DevMem& cmaps,
-                    const std::vector<int>& rng, const std::vector<double>& fl, int a, int b) -> cudaError_t {
+                    const std::vector<int>& rng, const std::vector<double>& fl, const DevMem& tc,
+                    const std::vector<int>& tc_rng, int a, int b) -> cudaError_t {
         auto one = [&](int lo, int hi, int tf) -> cudaError_t {
             if (hi <= lo) return cudaSuccess;
-            const int t0 = rng[lo], t1 = rng[hi];
+            const bool use_tc = tf && split;
+            const int t0 = use_tc ? tc_rng[lo] : rng[lo], t1 = use_tc ? tc_rng[hi] : rng[hi];
             ++h->launches;
             const int rec = h->profile ? prof_begin(h, st, 0, range_flops(fl, lo, hi)) : -1;
             cudaError_t e;
-            if (tf && split)
-                e = launch_gemm_tf32s(S, *split, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
+            if (use_tc)
+                e = launch_gemm_tf32s(S, *split, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tc.as<GemmTile>() + t0,
                                       cmaps.as<int>(), t1 - t0, tf == 2, st);
             else if (tf)
                 e = launch_gemm_tf32(S, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tiles.as<GemmTile>() + t0,
@@ -297,7 +315,7 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
         return one(std::max(a, G), b, 0);
     };
     auto runA = [&](int a, int b) -> cudaError_t {
-        return gemm(P.d_tasksA, P.d_segsA, P.d_tilesA, P.d_cmapsA, P.tileA_rng, P.flopsA_rng, a, b);
+        return gemm(P.d_tasksA, P.d_segsA, P.d_tilesA, P.d_cmapsA, P.tileA_rng, P.flopsA_rng, P.d_tcA, P.tcA_rng, a, b);
     };
     auto runB = [&](int a, int b) -> cudaError_t {
         const int o0 = P.combB_rng[a], o1 = P.combB_rng[b];
@@ -308,7 +326,7 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
         return e;
     };
     auto runC = [&](int a, int b) -> cudaError_t {
-        return gemm(P.d_tasksC, P.d_segsC, P.d_tilesC, P.d_cmapsC, P.tileC_rng, P.flopsC_rng, a, b);
+        return gemm(P.d_tasksC, P.d_segsC, P.d_tilesC, P.d_cmapsC, P.tileC_rng, P.flopsC_rng, P.d_tcC, P.tcC_rng, a, b);
     };
     // tensor-core phases read pre-split operands: x before phase A, the phase-B output before C
     const bool pre_split = prec > 0 && split && r0 < G;

@@ -89,6 +89,8 @@ struct Plan {
     double flops = 0.0;
     double flops_op[4] = {0, 0, 0, 0};
     DevMem d_tasksA, d_segsA, d_tilesA, d_cmapsA, d_outsB, d_termsB, d_tasksC, d_segsC, d_tilesC, d_cmapsC;
+    DevMem d_tcA, d_tcC;                     // tensor-core tile lists
+    std::vector<int> tcA_rng, tcC_rng;       // their ranges per (op, g)
     // diagonal (apply plans only)
     std::vector<DiagBlock> diag_blocks;
     std::vector<DiagTerm> diag_terms;

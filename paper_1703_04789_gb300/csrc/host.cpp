@@ -152,6 +152,24 @@ void GemmPlan::add_tiles(const TilePolicy& pol) {
     }
 }
 
+void GemmPlan::add_tc_tiles() {
+    tc_tiles.clear();
+    for (size_t t = 0; t < tasks.size(); ++t) {
+        const GemmTask& T = tasks[t];
+        for (int m0 = 0; m0 < T.M; m0 += 32)
+            for (int n0 = 0; n0 < T.N; n0 += 32) {
+                GemmTile g{};
+                g.task = static_cast<int>(t);
+                g.m0 = static_cast<int16_t>(m0);
+                g.n0 = static_cast<int16_t>(n0);
+                g.tm = static_cast<int16_t>(T.M - m0 < 32 ? T.M - m0 : 32);
+                g.tn = static_cast<int16_t>(T.N - n0 < 32 ? T.N - n0 : 32);
+                g.shape = 6;
+                tc_tiles.push_back(g);
+            }
+    }
+}
+
 // ---- MPOs -----------------------------------------------------------------------------------
 
 namespace {

@@ -47,7 +47,8 @@ __device__ __forceinline__ void region(const GemmTile& t, int& h, int& w) {
         case 2: h = 64; w = 4; break;
         case 3: h = 32; w = 8; break;
         case 4: h = 8; w = 32; break;
-        case 5: h = t.tm; w = t.tn; break;
+        case 5:
+        case 6: h = t.tm; w = t.tn; break;
         default: h = 16; w = 16; break;
     }
 }
@@ -163,7 +164,7 @@ __device__ __forceinline__ const float2* resolve_s(const SlotsF& F, uint64_t h) 
 }
 
 template <bool SPLIT3>
-__global__ void __launch_bounds__(128) k_gemm_tf32s(Slots S, SlotsF F, const GemmTask* __restrict__ tasks,
+__global__ void __launch_bounds__(128, 4) k_gemm_tf32s(Slots S, SlotsF F, const GemmTask* __restrict__ tasks,
                                                     const GemmSeg* __restrict__ segs, const GemmTile* __restrict__ tiles,
                                                     const int* __restrict__ cmaps, int n_tiles) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
