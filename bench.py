@@ -9,10 +9,11 @@ learned Davidson correction), checkpoint, training of the correction.
 One step = for each target, restore the checkpoint (untimed) and run one full two-site sweep
 (2K-3 steps of generalised Davidson with the projected H_eff/N_eff action, decimation to D,
 environment updates: every row of the hot path) in the fast form: all beta points and blocks in
-grouped launches with autotuned GEMM tiles, FP64.  Beside it, from the same checkpoints: the FP64
-plain form (one launch per beta point and phase, fixed tiles) for both targets, and the
-mixed-precision (3xTF32 H products, FP64 finish) and mixed-precision + learned-correction forms
-for the S=0 target, each with its energy difference to the plain form.
+grouped launches with autotuned GEMM tiles, the H part of the block products in 3xTF32 on the
+tensor cores until the Davidson residual is below 1e-5, then FP64.  Beside it, from the same
+checkpoints: the FP64 plain form (one launch per beta point and phase, fixed tiles) for both
+targets, and the all-FP64 fast form and the fast form with the learned correction for the S=0
+target, each with its energy difference to the plain form.
 
 Value = target-sweeps per second of the fast form (both targets' sweeps over their device time).
 
@@ -51,10 +52,11 @@ WORKLOAD = {
     "L": 24, "N": 24, "D": 256, "n_beta": 8, "U": 4.0, "targets": [[0, 0], [2, 2]], "site": 11,
     "mps": "seeded random (N,M)-symmetric MPS, inputs.random_mps(seed=2), canonicalised on the GPU",
     "davidson": "|r| < 1e-6 and |dtheta| < 1e-10, subspace 20, cap 200",
-    "forms": {"fast": "grouped launches over all beta points and blocks, autotuned GEMM tiles, FP64, diagonal correction",
+    "forms": {"fast": "grouped launches over all beta points and blocks, autotuned GEMM tiles, H part of the "
+                      "block products in 3xTF32 on the tensor cores until |r| < 1e-5, then FP64; diagonal correction",
               "fp64_plain": "one launch per beta point and phase, fixed tiles, FP64, diagonal correction",
-              "fast_3xtf32": "fast with the H part of the block products in 3xTF32 until |r| < 1e-5 or stagnation, then FP64",
-              "fast_3xtf32_learned": "fast_3xtf32 with the learned Davidson correction"},
+              "fast_fp64": "fast with every block product in FP64",
+              "fast_learned": "fast with the learned Davidson correction"},
     "l2": "flushed before every timed sweep (256 MiB write); environments of all bonds exceed L2",
 }
 
@@ -159,10 +161,10 @@ def _time_sweeps(dev, ckpt, steps, flush, torch):
 
 
 FORMS = {
-    "fast": dict(batched=True, autotune=True, precision="fp64", precond="diag"),
+    "fast": dict(batched=True, autotune=True, precision="3xtf32", precond="diag"),
     "fp64_plain": dict(batched=False, autotune=False, precision="fp64", precond="diag"),
-    "fast_3xtf32": dict(batched=True, autotune=True, precision="3xtf32", precond="diag"),
-    "fast_3xtf32_learned": dict(batched=True, autotune=True, precision="3xtf32", precond="learned"),
+    "fast_fp64": dict(batched=True, autotune=True, precision="fp64", precond="diag"),
+    "fast_learned": dict(batched=True, autotune=True, precision="3xtf32", precond="learned"),
 }
 
 
@@ -251,7 +253,7 @@ def run_ours(args):
         res_plain.append(_time_sweeps(d, h["ckpt"], 1, flush, torch))
         d.close()
     variants = {}
-    for form in ("fast_3xtf32", "fast_3xtf32_learned"):
+    for form in ("fast_fp64", "fast_learned"):
         d = _handle(form, hs[0]["twoM"], hs[0]["twoS"], params)
         r = _time_sweeps(d, hs[0]["ckpt"], 1, flush, torch)
         d.close()
@@ -271,7 +273,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 6), "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (H block products 3xTF32 until |r| < 1e-5, FP64 finish)", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
         "sweep_s": {"fast": {k: round(v, 4) for k, v in fast_mean.items()},
                     "fp64_plain": {k: round(v, 4) for k, v in plain_s.items()}},
@@ -358,7 +361,8 @@ def run_reference(args):
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(per_action * 1e3, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (H block products 3xTF32 until |r| < 1e-5, FP64 finish)", "data": "synthetic", "impl": "reference",
         "config": dict(WORKLOAD, step_note="reference step = one projected action of the S=0 target (bounded "
                                            "sample), scaled to a sweep by ACTIONS_PER_PLAIN_SWEEP"),
         "cpu_baseline": {"value": value, "unit": "sweeps/s", "kind": "oracle", "cores": os.cpu_count(),
