@@ -231,19 +231,26 @@ def run_ours(args):
         d.sweep(1)
     e2e_s = time.perf_counter() - t0
     e2e_value = len(hs) * world / e2e_s
-    # the dominant kernel at the middle site of the S=0 target: phases A and C of the action
-    # (k_gemm_f64), CUDA events on the handle's stream, warm
-    d0 = fast[0]
+    # the dominant kernel, k_gemm_f64, at the middle site of the S=0 target: phases A and C of the
+    # FP64 action (CUDA events on the handle's stream, warm); and the same action with the H part
+    # on the tensor cores (the fast form's first Davidson stage)
     site = WORKLOAD["site"]
-    lay = d0.x_layout(site)
-    xs = torch.tensor(np.random.default_rng(0).standard_normal(lay["n_x"]), device="cuda")
-    ys, zs = torch.empty_like(xs), torch.empty_like(xs)
-    d0.apply_heff(site, xs, ys, zs)
-    torch.cuda.synchronize()
-    phase = np.mean([d0.apply_heff_timed(site, xs, ys, zs) for _ in range(5)], axis=0)
-    fl_site = d0.apply_flops(site)
+
+    def middle_site_phases(dev):
+        lay = dev.x_layout(site)
+        xs = torch.tensor(np.random.default_rng(0).standard_normal(lay["n_x"]), device="cuda")
+        ys, zs = torch.empty_like(xs), torch.empty_like(xs)
+        dev.apply_heff(site, xs, ys, zs)
+        torch.cuda.synchronize()
+        return np.mean([dev.apply_heff_timed(site, xs, ys, zs) for _ in range(5)], axis=0), dev.apply_flops(site)
+
+    phase_tc, _ = middle_site_phases(fast[0])
     for d in fast:
         d.close()
+    d64 = _handle("fast_fp64", hs[0]["twoM"], hs[0]["twoS"])
+    d64.set_mps(*hs[0]["ckpt"][:2], center=hs[0]["ckpt"][2])
+    phase, fl_site = middle_site_phases(d64)
+    d64.close()
 
     # the FP64 plain form (one sweep per target) and the mixed-precision / learned variants
     # (one sweep of the S=0 target), all from the same checkpoints
@@ -299,6 +306,11 @@ def run_ours(args):
                      "traffic_note": "bytes per launch (mean of the phase-A and phase-C launches), ncu capture in "
                                      "profiles/k_gemm_f64_hubbard_L24_D256.md",
                      "phase_ms": [round(float(v), 4) for v in phase],
+                     "tensor_core_action": {
+                         "phase_ms": [round(float(v), 4) for v in phase_tc],
+                         "algorithmic_tflops_A_C": round(float(fl_site[0] + fl_site[2]) / ((phase_tc[1] + phase_tc[3]) * 1e-3)
+                                                         / 1e12, 4),
+                         "speedup_A_C_vs_fp64": round(float((phase[1] + phase[3]) / (phase_tc[1] + phase_tc[3])), 3)},
                      "sweep_gemms": {"achieved": round(g_fl / (g_ms * 1e-3) / 1e12, 6) if g_ms > 0 else 0.0,
                                      "frac": round(g_fl / (g_ms * 1e-3) / 1e12 / peak, 4) if g_ms > 0 and peak else None,
                                      "launches": g_n, "avg_launch_ms": round(g_ms / max(1, g_n), 5),
@@ -362,7 +374,7 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(per_action * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (H block products 3xTF32 until |r| < 1e-5, FP64 finish)", "data": "synthetic", "impl": "reference",
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": dict(WORKLOAD, step_note="reference step = one projected action of the S=0 target (bounded "
                                            "sample), scaled to a sweep by ACTIONS_PER_PLAIN_SWEEP"),
         "cpu_baseline": {"value": value, "unit": "sweeps/s", "kind": "oracle", "cores": os.cpu_count(),
