@@ -39,11 +39,12 @@ def main():
     ap.add_argument("--site", type=int, default=11)
     ap.add_argument("--profile-sweep", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "3xtf32"])
     args = ap.parse_args()
     import torch
     from . import build
     build.build()
-    h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune)[0]
+    h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune, precision=args.precision)[0]
     dev = h["dev"]
     lay = dev.x_layout(args.site)
     x = torch.tensor(np.random.default_rng(0).standard_normal(lay["n_x"]), device="cuda")
