@@ -455,86 +455,7 @@ __device__ int jacobi_cta(double* A, int lda, double* V, int ldv, int n, int max
     return sweep;
 }
 
-// ---- Ritz step of the generalised Davidson solver (one CTA, m <= 32) ---------------------------
 constexpr int kRitzMax = 32;
-
-__global__ void __launch_bounds__(256) k_ritz(const double* __restrict__ h, const double* __restrict__ nm, int ldm,
-                                              int m, double eps_metric, double* __restrict__ coef,
-                                              double* __restrict__ scal) {
-    // 5 buffers of 32 x 32: Hs (h, later H'), Ns (n -> mu), Qn (metric vectors, later X^T H X),
-    // X (canonical basis), TC (H X, later the Ritz vectors of H')
-    __shared__ double Hs[kRitzMax * kRitzMax], Ns[kRitzMax * kRitzMax], Qn[kRitzMax * kRitzMax];
-    __shared__ double X[kRitzMax * kRitzMax], TC[kRitzMax * kRitzMax];
-    __shared__ double cs_sh[kRitzMax + 2], red_sh[40];
-    __shared__ int pq_sh[kRitzMax + 2];
-    __shared__ int keep_idx[kRitzMax];
-    __shared__ int nkeep, jmin;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    // stored column j holds the entries i <= j; mirror into symmetric matrices
-    for (int e = tid; e < m * m; e += nt) {
-        const int i = e / m, j = e - i * m;
-        const int lo = i < j ? i : j, hi = i < j ? j : i;
-        Hs[i * kRitzMax + j] = h[hi * ldm + lo];
-        Ns[i * kRitzMax + j] = nm[hi * ldm + lo];
-    }
-    __syncthreads();
-    jacobi_cta(Ns, kRitzMax, Qn, kRitzMax, m, 40, cs_sh, pq_sh, red_sh);
-    if (tid == 0) {
-        double mx = 0.0;
-        for (int i = 0; i < m; ++i) mx = fmax(mx, Ns[i * kRitzMax + i]);
-        int k = 0;
-        if (mx > 0.0)
-            for (int i = 0; i < m; ++i)
-                if (Ns[i * kRitzMax + i] > eps_metric * mx) keep_idx[k++] = i;
-        nkeep = k;
-    }
-    __syncthreads();
-    const int k = nkeep;
-    if (k == 0) {
-        if (tid == 0) { scal[0] = 0.0; scal[1] = 0.0; }
-        return;
-    }
-    for (int e = tid; e < m * k; e += nt) {  // X = Qn[:, keep] / sqrt(mu)
-        const int i = e / k, c = e - i * k;
-        const int q = keep_idx[c];
-        X[i * kRitzMax + c] = Qn[i * kRitzMax + q] / sqrt(Ns[q * kRitzMax + q]);
-    }
-    __syncthreads();
-    for (int e = tid; e < m * k; e += nt) {  // TC = H X
-        const int i = e / k, c = e - i * k;
-        double acc = 0.0;
-        for (int l = 0; l < m; ++l) acc = fma(Hs[i * kRitzMax + l], X[l * kRitzMax + c], acc);
-        TC[i * kRitzMax + c] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < k * k; e += nt) {  // Qn = X^T TC
-        const int a = e / k, b = e - a * k;
-        double acc = 0.0;
-        for (int l = 0; l < m; ++l) acc = fma(X[l * kRitzMax + a], TC[l * kRitzMax + b], acc);
-        Qn[a * kRitzMax + b] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < k * k; e += nt) {  // Hs = symmetrised H'
-        const int a = e / k, b = e - a * k;
-        Hs[a * kRitzMax + b] = 0.5 * (Qn[a * kRitzMax + b] + Qn[b * kRitzMax + a]);
-    }
-    __syncthreads();
-    jacobi_cta(Hs, kRitzMax, TC, kRitzMax, k, 40, cs_sh, pq_sh, red_sh);
-    if (tid == 0) {
-        int best = 0;
-        for (int i = 1; i < k; ++i)
-            if (Hs[i * kRitzMax + i] < Hs[best * kRitzMax + best]) best = i;
-        jmin = best;
-        scal[0] = Hs[best * kRitzMax + best];
-        scal[1] = static_cast<double>(k);
-    }
-    __syncthreads();
-    for (int i = tid; i < m; i += nt) {
-        double acc = 0.0;
-        for (int c = 0; c < k; ++c) acc = fma(X[i * kRitzMax + c], TC[c * kRitzMax + jmin], acc);
-        coef[i] = acc;
-    }
-}
 
 // ---- incremental Ritz step --------------------------------------------------------------------
 // Keeps, across the iterations of one Davidson solve, an n-orthonormal coefficient basis X
@@ -1099,12 +1020,6 @@ cudaError_t launch_basis_rotate(const double* src, int64_t ld, int m, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_ritz(const double* h, const double* nmat, int ldm, int m, double eps_metric, double* coef,
-                        double* scal, cudaStream_t st) {
-    if (m > kRitzMax) return cudaErrorInvalidValue;
-    k_ritz<<<1, 256, 0, st>>>(h, nmat, ldm, m, eps_metric, coef, scal);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_ritz_inc(const double* h, const double* nmat, int ldm, int m, int reset, double eps_metric,
                             RitzState* state, double* coef, double* scal, cudaStream_t st) {

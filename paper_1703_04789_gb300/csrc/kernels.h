@@ -54,14 +54,11 @@ cudaError_t launch_gemv(const double* V, int64_t ldv, int m, const double* c, in
 cudaError_t launch_basis_rotate(const double* src, int64_t ld, int m, const double* Q, int ldq, int k,
                                 int64_t n, double* dst, cudaStream_t st);
 
-// Davidson Ritz step on the device (one CTA): symmetrise h, n (m x m, leading dim ldm),
-// canonical orthogonalisation of n, lowest Ritz pair.  Writes coef[0..m) and
-// scal[0] = theta, scal[1] = number of kept metric directions (0 = singular).
-cudaError_t launch_ritz(const double* h, const double* nmat, int ldm, int m, double eps_metric, double* coef,
-                        double* scal, cudaStream_t st);
-
-// Incremental Ritz step (one CTA of 128 threads): state kept across iterations of one solve; reset != 0
-// rebuilds it from the m stored columns.  Same outputs as launch_ritz.
+// Incremental Ritz step of the Davidson solver (one CTA of 128 threads) on the stored subspace
+// matrices h, n (m x m, leading dim ldm, upper triangles column by column): lowest Ritz pair in the
+// range of n kept above eps_metric * max diag(n).  The state is kept across the iterations of one
+// solve; reset != 0 rebuilds it from the m stored columns.  Writes coef[0..m) and scal[0] = theta,
+// scal[1] = number of kept metric directions (0 = singular).
 struct RitzState {
     static constexpr int kR = 32;
     double X[kR * kR];   // n-orthonormal coefficient basis, X[i + j*kR]
