@@ -310,9 +310,34 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
             return e;
         };
         if (prec == 0) return one(a, b, 0);
-        cudaError_t e = one(a, std::min(b, G), prec);
+        if (!split || b <= G || a >= G) {
+            cudaError_t e = one(a, std::min(b, G), prec);
+            if (e != cudaSuccess) return e;
+            return one(std::max(a, G), b, 0);
+        }
+        // H part on the tensor cores on this stream, N part (FP64 pipe) concurrently on the second
+        // stream; the outputs are disjoint
+        if (!h->aux_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->aux_join, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventRecord(h->aux_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->aux_fork, 0);
         if (e != cudaSuccess) return e;
-        return one(std::max(a, G), b, 0);
+        {
+            const cudaStream_t main_st = st;
+            st = h->aux_stream;  // `one` launches on st
+            e = one(std::max(a, G), b, 0);
+            st = main_st;
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaEventRecord(h->aux_join, h->aux_stream);
+        if (e != cudaSuccess) return e;
+        e = one(a, std::min(b, G), prec);
+        if (e != cudaSuccess) return e;
+        return cudaStreamWaitEvent(st, h->aux_join, 0);
     };
     auto runA = [&](int a, int b) -> cudaError_t {
         return gemm(P.d_tasksA, P.d_segsA, P.d_tilesA, P.d_cmapsA, P.tileA_rng, P.flopsA_rng, P.d_tcA, P.tcA_rng, a, b);
@@ -1399,6 +1424,12 @@ spmps_status spmps_destroy(spmps_handle h) {
     h->Lenv.clear();
     h->Renv.clear();
     h->A.clear();
+    if (h->aux_stream) {
+        cudaStreamSynchronize(h->aux_stream);
+        cudaStreamDestroy(h->aux_stream);
+    }
+    if (h->aux_fork) cudaEventDestroy(h->aux_fork);
+    if (h->aux_join) cudaEventDestroy(h->aux_join);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return SPMPS_OK;

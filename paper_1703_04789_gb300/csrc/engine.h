@@ -120,6 +120,10 @@ struct spmps_t {
     std::string err;
     int device = 0;
     cudaStream_t stream = nullptr;
+    // second stream of the mixed-precision action: the FP64 N_eff products run on it while the
+    // tensor-core H products run on the action's stream (created on first use)
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
     std::vector<double> beta, cg;
 
     bool has_ham = false, has_mps = false;
