@@ -113,6 +113,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time (replicas run independently; the job is done when all are)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 def _setup(args):
     """Checkpoints after the warm-up sweeps (batched FP64 form, harvesting training pairs for the
     learned correction) and the trained correction; returns per-target dicts and its parameters."""
@@ -217,19 +233,15 @@ def run_ours(args):
         d.profile(False)
     launches = sum(d.stats()["launches"] for d in fast) - launches0
     apply_flops = sum(d.stats()["apply_flops_total"] - f0 for d, f0 in zip(fast, flops0))
-    total_ms = sum(sum(r["ms"]) for r in res_fast)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = args.steps * len(hs) * world / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(sum(r["ms"]) for r in res_fast), "cuda")
+    value = whole_job_rate(args.steps * len(hs), world, total_ms)
 
     # end to end through the host C ABI: checkpoint upload (host -> device), sweep, energy read-back
     t0 = time.perf_counter()
     for d, h in zip(fast, hs):
         d.set_mps(*h["ckpt"][:2], center=h["ckpt"][2])
         d.sweep(1)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks((time.perf_counter() - t0) * 1e3, "cuda") * 1e-3
     e2e_value = len(hs) * world / e2e_s
     # the dominant kernel, k_gemm_f64, at the middle site of the S=0 target: phases A and C of the
     # FP64 action (CUDA events on the handle's stream, warm); and the same action with the H part
