@@ -62,13 +62,18 @@ typedef struct {
     int dav_max_sub;    /* Davidson subspace size before restart (default 20, max 32)         */
     int dav_max_iter;   /* Davidson iteration cap per two-site step (default 200)             */
     int device;         /* CUDA device ordinal (default 0)                                    */
-    int jacobi_smem_max; /* decimation blocks up to this size are diagonalised in shared memory,
-                            larger ones in global memory (default and maximum 112; 0 = default) */
+    int jacobi_smem_max; /* decimation blocks handled by one CTA (dimension <= 64 or > 256) up to
+                            this size are diagonalised in shared memory, larger ones in global
+                            memory (default and maximum 112; 0 = default); blocks of dimension
+                            65..256 always run on an 8-CTA thread-block cluster */
     int precision;      /* bulk H_eff x block products: 0 = FP64 (default), 1 = TF32, 2 = 3xTF32
                            (tensor cores, FP32 accumulation).  N_eff x, environments, Davidson and
-                           decimation stay FP64; with 1 or 2 each Davidson solve converges first
-                           with reduced-precision actions, then switches to FP64 actions in the
-                           same subspace and converges to the FP64 tolerance. */
+                           decimation stay FP64; with 1 or 2 each Davidson solve starts with
+                           reduced-precision actions (keeping only subspace directions whose
+                           N-norm is well above the precision of the products) and switches to
+                           FP64 actions in the same subspace once |r| < 1e-5 (3xTF32) or 1e-3
+                           (TF32; also when |r| stagnates), at the latest at half of dav_max_iter,
+                           then converges to the FP64 tolerance. */
     int autotune;       /* 1: the first projected-action plan of each site times the candidate
                            tile policies of the block GEMMs (phases A and C separately, CUDA
                            events, a few actions on scratch vectors) and keeps the fastest for
@@ -263,9 +268,8 @@ spmps_status spmps_seniority(spmps_handle h, double* value);
 spmps_status spmps_stats(spmps_handle h, int64_t* counts, double* values);
 
 /* Davidson iterations of the last spmps_sweep call: *iterations counts every iteration, and
- * *refine_iterations the part spent in the FP64 refinement stage that follows a TF32 / 3xTF32
- * stage (0 with precision 0).  Both are reset when spmps_sweep starts.  Either pointer may be
- * NULL. */
+ * *refine_iterations those after the switch from the TF32 / 3xTF32 action to the FP64 action
+ * (0 with precision 0).  Both are reset when spmps_sweep starts.  Either pointer may be NULL. */
 spmps_status spmps_davidson_stats(spmps_handle h, int64_t* iterations, int64_t* refine_iterations);
 
 /* Copy the current MPS to host memory (checkpoint).  First call with sites == NULL: fills
