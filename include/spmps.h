@@ -46,7 +46,7 @@ typedef enum {
     SPMPS_ERR_CUDA = 6,             /* CUDA runtime error (message in spmps_last_error)    */
     SPMPS_ERR_NAN = 7,              /* NaN or Inf detected in a result                     */
     SPMPS_ERR_STATE = 8,            /* call out of order (e.g. no Hamiltonian or MPS set)  */
-    SPMPS_ERR_UNSUPPORTED = 9       /* valid request this build does not implement         */
+    SPMPS_ERR_UNSUPPORTED = 9       /* valid request the library does not implement       */
 } spmps_status;
 
 typedef struct {
