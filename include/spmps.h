@@ -71,9 +71,10 @@ typedef struct {
                            decimation stay FP64; with 1 or 2 each Davidson solve starts with
                            reduced-precision actions (keeping only subspace directions whose
                            N-norm is well above the precision of the products) and switches to
-                           FP64 actions in the same subspace once |r| < 1e-5 (3xTF32) or 1e-3
-                           (TF32; also when |r| stagnates), at the latest at half of dav_max_iter,
-                           then converges to the FP64 tolerance. */
+                           FP64 actions in the same subspace once |r| < max(1e-5, 1e-6 |theta|)
+                           (3xTF32) or max(1e-3, 1e-3 |theta|) (TF32; also when |r| stagnates), at
+                           the latest at half of dav_max_iter, then converges to the FP64
+                           tolerance. */
     int autotune;       /* 1: the first projected-action plan of each site times the candidate
                            tile policies of the block GEMMs (phases A and C separately, CUDA
                            events, a few actions on scratch vectors) and keeps the fastest for

@@ -348,7 +348,11 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         // too; 3xTF32 reaches its tolerance well above its floor
         const bool stagnated = h->apply_precision == 1 && it - best_it >= kStagnation;
         // and every solve finishes in FP64: switch at half the iteration cap at the latest
-        if (!switched && (rn < switch_tol || stagnated || it >= cap / 2)) {
+        // the error of the reduced-precision products grows with the scale of H: the switch level
+        // is relative to |theta| (about 1e-6 for 3xTF32 and 1e-3 for TF32) where that is above
+        // the absolute one
+        const double switch_at = std::max(switch_tol, (h->apply_precision == 1 ? 1e-3 : 1e-6) * std::fabs(theta));
+        if (!switched && (rn < switch_at || stagnated || it >= cap / 2)) {
             // the new direction (column m) is applied in FP64 below
             st = switch_to_fp64(it);
             if (st != SPMPS_OK) return st;
