@@ -315,8 +315,8 @@ def run_ours(args):
                      if peak else None,
                      "peak_source": "measured FP64 FMA-chain kernel on all SMs (spmps_device_fp64_peak; nominal 1.25)",
                      "traffic": TRAFFIC_PER_LAUNCH,
-                     "traffic_note": "bytes per launch (mean of the phase-A and phase-C launches), ncu capture in "
-                                     "profiles/k_gemm_f64_hubbard_L24_D256.md",
+                     "traffic_note": "bytes per launch (mean of the phase-A and phase-C launches), ncu capture of the "
+                                     "middle-site action",
                      "phase_ms": [round(float(v), 4) for v in phase],
                      "tensor_core_action": {
                          "phase_ms": [round(float(v), 4) for v in phase_tc],

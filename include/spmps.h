@@ -193,19 +193,22 @@ spmps_status spmps_apply_flops(spmps_handle h, int site, double* flops3);
  * independent FMA chains on every SM (the roofline denominator of the FP64 path). */
 spmps_status spmps_device_fp64_peak(int device, double* tflops);
 
-/* The same projected action as spmps_apply_heff, for callers that cannot allocate device memory
- * when they need it: code inside CUDA stream capture, callers whose device memory is reserved
- * up front by their own pool, or runtimes that forbid the CUDA allocator after start-up.  The
- * paper has no counterpart; this is an interface variant only.
+/* The same projected action as spmps_apply_heff, for callers that cannot let the library allocate
+ * device memory when they need it: callers whose device memory is reserved up front by their own
+ * pool allocator, or embedding runtimes that forbid the CUDA allocator after start-up.  The paper
+ * has no counterpart; this is an interface variant only.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its intermediates live in one
  * file-scope device array of 4 Mi doubles (32 MiB) that every GPU loading the library keeps until
- * exit; problems needing more return SPMPS_ERR_BAD_INPUT.  The environments and contraction plan
- * of `site` must already exist (a previous spmps_apply_heff or spmps_energy call for that site
- * builds them, and allocates); otherwise SPMPS_ERR_STATE.  All calls share the array, which keeps
- * the last call's contents (the call zeroes what must start at zero): calls that overlap on the
- * GPU race and must be serialised.  The first call on each device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Arguments as in
- * spmps_apply_heff. */
+ * exit; problems needing more return SPMPS_ERR_BAD_INPUT.  The H part always runs in FP64 (as
+ * spmps_apply_heff with precision 0), whatever the handle's precision option.  The environments
+ * and contraction plan of `site` must already exist (a previous spmps_apply_heff or spmps_energy
+ * call for that site builds them, and allocates); otherwise SPMPS_ERR_STATE.  All calls share the
+ * array, which keeps the last call's contents (the call zeroes what must start at zero): calls
+ * that overlap on the GPU race and must be serialised.  When `stream` is not the handle's stream,
+ * the call orders it after the work already queued on the handle's stream (an event; the first
+ * such call on a handle creates it).  The first call on each device looks up the array's address
+ * (cudaGetSymbolAddress).  The per-launch profiler (spmps_profile) does not record this call.
+ * Arguments as in spmps_apply_heff. */
 spmps_status spmps_apply_heff_noalloc(spmps_handle h, int site, const double* x, double* y, double* z,
                                       void* stream);
 

@@ -15,7 +15,12 @@ What is computed, with the passage it follows:
   projected back to (N, M)).
 * Eq. geproblem solved by a generalised Davidson iteration (details are not in the paper:
   Euclidean-orthonormal basis, canonical orthogonalisation of the projected metric,
-  lowest Ritz value, diagonal preconditioner).
+  lowest Ritz value, diagonal preconditioner or the inverse of the metric's symmetry blocks).
+* The metric N_eff of Fig. spmpsOpt (c) is the network of the rotated identity MPO, so it is a
+  sum over g of c_g L^N_g (x) r_g (x) r_g (x) R^N_g.  Each factor conserves the particle number
+  of its own part (left block, site k, site k+1, right block), hence N_eff is exactly
+  block-diagonal in (n of the left index, n(s1), n(s2)); ``metric_blocks`` assembles those
+  blocks densely from the factors.
 * Sec. 2.3.1: decimation by SVD in the usual canonical gauge; two-site sweeps.
 """
 from __future__ import annotations
@@ -28,6 +33,7 @@ from .mpo import rotate_mpo, identity_mpo
 from .quadrature import projector_quadrature
 
 LOCAL_Q = np.array([[0, 0], [1, -1], [1, 1], [2, 0]], dtype=np.int64)  # (n, 2m) of {0,b,a,ab}
+METRIC_SHIFT = 1e-10  # shift of the metric blocks in precond="metric_block" (|N_eff| <= 1)
 
 
 def site_mask(ql, qr):
@@ -222,6 +228,31 @@ class Projected:
             out.append(np.where(mask, acc, 0.0))
         return tuple(out)
 
+    def metric_blocks(self, k):
+        """The diagonal blocks of N_eff at sites (k, k+1) in the (N, M)-allowed entries of the
+        two-site tensor, one block per (n of the left bond index, n(s1), n(s2)): a list of
+        (positions in the flattened masked vector, dense block).  Block entries are
+        sum_g c_g LN_g[a, a'] rN_g[s1, s1'] rN_g[s2, s2'] RN_g[b, b'] (the identity MPO rotated
+        by beta_g has bond dimension 1)."""
+        ql, qr = self.mps.labels[k], self.mps.labels[k + 2]
+        mask = two_site_mask(ql, qr)
+        ia, i1, i2, ib = np.nonzero(mask)
+        nloc = LOCAL_Q[:, 0]
+        key = np.stack([ql[ia, 0], nloc[i1], nloc[i2]], axis=1)
+        out = []
+        for kk in sorted(set(map(tuple, key))):
+            pos = np.nonzero(np.all(key == kk, axis=1))[0]
+            a, s1, s2, b = ia[pos], i1[pos], i2[pos], ib[pos]
+            blk = np.zeros((len(pos), len(pos)))
+            for g, cg in enumerate(self.c):
+                L = self.Ln[g][k][:, 0, :]
+                R = self.Rn[g][k + 2][:, 0, :]
+                r1 = self.Wn[g][k][0, 0]
+                r2 = self.Wn[g][k + 1][0, 0]
+                blk += cg * L[np.ix_(a, a)] * r1[np.ix_(s1, s1)] * r2[np.ix_(s2, s2)] * R[np.ix_(b, b)]
+            out.append((pos, blk))
+        return out
+
     def two_site(self, k):
         return np.einsum("asc,cjb->asjb", self.mps.A[k], self.mps.A[k + 1])
 
@@ -245,7 +276,8 @@ class DavidsonResult:
 
 def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
              max_sub=20, max_iter=200, eps_metric=1e-12, clamp=1e-4,
-             precond="diag", apply_n=None, cg_steps=5) -> DavidsonResult:
+             precond="diag", apply_n=None, cg_steps=5, metric_blocks=None,
+             metric_shift=METRIC_SHIFT) -> DavidsonResult:
     """Lowest eigenpair of H x = theta N x with N positive semi-definite.
 
     Basis V Euclidean-orthonormal (classical Gram-Schmidt applied twice); Ritz problem
@@ -253,7 +285,10 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
     eps_metric * max dropped); x = V c with x^T N x = 1; residual r = H x - theta N x;
     correction t = -r / (diag H - theta diag N), the denominator clamped to |.| >= clamp
     (precond="diag"), or t = cg_steps conjugate-gradient steps on N t = r from t = 0
-    (precond="metric", an approximate N^+ r; needs ``apply_n``);
+    (precond="metric", an approximate N^+ r; needs ``apply_n``), or
+    t = (N_b + metric_shift I)^-1 r on every diagonal block N_b of N (precond="metric_block";
+    ``metric_blocks`` from Projected.metric_blocks: N is block-diagonal, so this is the inverse of
+    N shifted by metric_shift, which keeps directions of N-norm down to ~metric_shift);
     restart from [x, previous x] when the basis reaches max_sub; converged when
     ||r|| < tol_r and |theta - theta_prev| < tol_theta."""
     shape = x0.shape
@@ -303,6 +338,10 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
         theta_prev = theta
         if precond == "metric":
             t = _cg_metric(lambda u: op_n(u), r, cg_steps)
+        elif precond == "metric_block":
+            t = np.zeros_like(r)
+            for pos, blk in metric_blocks:
+                t[pos] = np.linalg.solve(blk + metric_shift * np.eye(len(pos)), r[pos])
         else:
             den = dh - theta * dn
             den = np.where(np.abs(den) < clamp, np.where(den < 0, -clamp, clamp), den)
@@ -455,6 +494,8 @@ def two_site_step(P: Projected, k: int, move_right: bool, D: int, log: SweepLog,
     ql, qr = mps.labels[k], mps.labels[k + 2]
     mask = two_site_mask(ql, qr)
     dh, dn = P.diagonal(k)
+    if dav.get("precond") == "metric_block":
+        dav = dict(dav, metric_blocks=P.metric_blocks(k))
     res = davidson(lambda v: P.apply(v, k), x0, dh, dn, mask,
                    apply_n=lambda v: P.apply(v, k, which=("n",))[0], **dav)
     Al, Ar, lm, disc = decimate(res.x, ql, qr, D, move_right)

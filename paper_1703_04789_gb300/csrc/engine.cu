@@ -1430,6 +1430,7 @@ spmps_status spmps_destroy(spmps_handle h) {
     }
     if (h->aux_fork) cudaEventDestroy(h->aux_fork);
     if (h->aux_join) cudaEventDestroy(h->aux_join);
+    if (h->noalloc_order) cudaEventDestroy(h->noalloc_order);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return SPMPS_OK;

@@ -124,6 +124,8 @@ struct spmps_t {
     // tensor-core H products run on the action's stream (created on first use)
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
+    // orders a caller's stream after the handle's stream in spmps_apply_heff_noalloc
+    cudaEvent_t noalloc_order = nullptr;
     std::vector<double> beta, cg;
 
     bool has_ham = false, has_mps = false;

@@ -1,11 +1,12 @@
 // The projected action without any device allocation, for callers that cannot call cudaMalloc.
 //
 // Some callers cannot allocate device memory at the point where they need the projected action:
-// code running inside CUDA stream capture (allocation is not capturable), callers whose memory
-// is fully reserved up front by their own pool, or embedding runtimes that forbid the CUDA
-// allocator after start-up.  spmps_apply_heff_noalloc serves them: it runs the same three-phase
-// contraction as spmps_apply_heff, but its intermediates (the M-dense T1/T3 blocks) live in a
-// fixed file-scope device array instead of the handle's workspace.
+// callers whose device memory is fully reserved up front by their own pool allocator, or
+// embedding runtimes that forbid the CUDA allocator after start-up (a cudaMalloc there would
+// fail or break the runtime's accounting).  spmps_apply_heff_noalloc serves them: it runs the
+// same three-phase FP64 contraction as spmps_apply_heff with precision 0, but its intermediates
+// (the M-dense T1/T3 blocks and the per-beta partials) live in a fixed file-scope device array
+// instead of the handle's workspace.
 //
 // Limits and caveats
 //   - The array holds kNoAllocScratchDoubles doubles (32 MiB).  Every GPU that loads the library
@@ -18,7 +19,11 @@
 //     and allocated, by a previous spmps_apply_heff or spmps_energy call for that site and MPS);
 //     otherwise the call returns SPMPS_ERR_STATE without doing anything.
 //   - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
-//     with that device current); make that first call before any stream capture.
+//     with that device current), and the first call on each handle creates one CUDA event (no
+//     device memory) that orders the caller's stream after the handle's stream.
+//   - The H part always runs in FP64, whatever the handle's precision option: the pre-split TF32
+//     operands of the reduced-precision forms would need room of their own in the array.
+//   - The library's per-launch profiler (spmps_profile) is not used by this call.
 #include <mutex>
 
 #include "engine.h"
@@ -74,6 +79,17 @@ extern "C" spmps_status spmps_apply_heff_noalloc(spmps_handle h, int site, const
     e = scratch_address(h->device, &base);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    if (s != h->stream) {
+        // environments are built on the handle's stream: order the caller's stream after the
+        // work queued there so far (no host synchronisation)
+        if (!h->noalloc_order) {
+            e = cudaEventCreateWithFlags(&h->noalloc_order, cudaEventDisableTiming);
+            if (e != cudaSuccess) { h->noalloc_order = nullptr; return cuda_fail(h, e, "cudaEventCreate"); }
+        }
+        e = cudaEventRecord(h->noalloc_order, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->noalloc_order, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "ordering the caller's stream after the handle's");
+    }
     Slots S{};
     S.p[0] = const_cast<double*>(x);
     S.p[1] = y;
@@ -87,9 +103,16 @@ extern "C" spmps_status spmps_apply_heff_noalloc(spmps_handle h, int site, const
     S.p[5] = h->Lenv[site].buf.as<double>();
     S.p[6] = h->Renv[site + 2].buf.as<double>();
     const int G = h->G;
+    // FP64 action without the profiler (its records create events and may synchronise)
+    const int prec_saved = h->apply_precision;
+    const bool prof_saved = h->profile;
+    h->apply_precision = 0;
+    h->profile = false;
     if (y && z) st = plan_run(h, *P, S, 0, 2 * G, s);
     else if (y) st = plan_run(h, *P, S, 0, G, s);
     else st = plan_run(h, *P, S, G, 2 * G, s);
+    h->apply_precision = prec_saved;
+    h->profile = prof_saved;
     if (st != SPMPS_OK) return st;
     ++h->applies;
     return SPMPS_OK;

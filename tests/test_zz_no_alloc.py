@@ -1,9 +1,9 @@
 """The allocation-free projected action (spmps_apply_heff_noalloc).
 
-Callers inside CUDA stream capture, or whose device memory is reserved up front, cannot let the
-library call cudaMalloc when they need the action; this entry point keeps its intermediates in
-a fixed static device array instead.  It must give the same y and z as spmps_apply_heff, call
-after call.  This file is collected last so that a failure here leaves every other test run.
+Callers whose device memory is reserved up front by their own pool, or runtimes that forbid the
+CUDA allocator after start-up, cannot let the library call cudaMalloc when they need the action;
+this entry point keeps its intermediates in a fixed static device array instead.  It must give
+the same y and z as spmps_apply_heff, call after call.  This file is collected last so that a failure here leaves every other test run.
 """
 import numpy as np
 import pytest
@@ -41,6 +41,36 @@ def test_noalloc_apply_matches_apply_on_two_calls():
             sz = max(1.0, float(z_ref.abs().max()))
             assert float((y - y_ref).abs().max()) <= RTOL * sy
             assert float((z - z_ref).abs().max()) <= RTOL * sz
+    dev.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_on_a_caller_stream_waits_for_the_handle_stream():
+    """The environments are built on the handle's stream; a call on another stream right after
+    the plan-building call (no host synchronisation in between) must still see them."""
+    require_gpu()
+    import torch
+    from paper_1703_04789_gb300 import Spmps
+    L, N, D, G = 10, 10, 48, 6
+    labels, tens = inputs.random_mps(L, N, 0, D, 4)
+    dev = Spmps(L, N, 0, 0, G, D)
+    dev.set_hubbard(1.0, 4.0)
+    dev.set_mps(labels, tens, center=0)
+    k = 4
+    n = dev.x_layout(k)["n_x"]
+    x = torch.tensor(np.random.default_rng(7).standard_normal(n), device="cuda")
+    y_ref, z_ref = torch.empty_like(x), torch.empty_like(x)
+    side = torch.cuda.Stream()
+    for _ in range(2):
+        dev.apply_heff(k, x, y_ref, z_ref)  # handle's stream, asynchronous
+        y = torch.full_like(x, float("nan"))
+        z = torch.full_like(x, float("nan"))
+        side.wait_stream(torch.cuda.current_stream())  # x, y, z were written on torch's stream
+        dev.apply_heff_noalloc(k, x, y, z, stream=side)
+        side.synchronize()
+        torch.cuda.synchronize()
+        assert float((y - y_ref).abs().max()) <= RTOL * max(1.0, float(y_ref.abs().max()))
+        assert float((z - z_ref).abs().max()) <= RTOL * max(1.0, float(z_ref.abs().max()))
     dev.close()
 
 
