@@ -55,7 +55,16 @@ typedef struct {
     int precond;        /* Davidson correction: 0 = diagonal (default), 1 = metric CG,
                            2 = learned (spmps_mlp_*; the diagonal correction is its fallback),
                            3 = Olsen: the diagonal correction plus eps M^-1 N x with eps making
-                           it N-orthogonal to x (M = diag H - theta diag N) */
+                           it N-orthogonal to x (M = diag H - theta diag N),
+                           4 = metric blocks: t = (N_eff + s I)^-1 r with s = 1e-7.  N_eff is the
+                           network of the rotated identity MPO (Fig. spmpsOpt (c)); every factor
+                           conserves the particle number of its part, so N_eff is exactly
+                           block-diagonal in (N of the left bond index, n(s1), n(s2)).  The blocks
+                           are assembled densely and factorised (FP64 Cholesky) once per two-site
+                           step.  The converged x, defined modulo ker N_eff, is replaced by the
+                           representative (N_eff + s I)^-1 N_eff x before decimation.  Blocks above
+                           metric_max_dim keep the diagonal correction (and x there); all of them
+                           do when the factors would exceed 8 GB or a pivot is not positive. */
     int cg_steps;       /* CG steps on N_eff t = r for precond == 1 (default 5)               */
     double dav_tol_r;   /* Davidson residual norm tolerance (default 1e-6)                    */
     double dav_tol_theta; /* Davidson eigenvalue change tolerance (default 1e-10)             */
@@ -79,6 +88,11 @@ typedef struct {
                            tile policies of the block GEMMs (phases A and C separately, CUDA
                            events, a few actions on scratch vectors) and keeps the fastest for
                            that site; 0 (default): the fixed least-padding policy. */
+    int metric_max_dim; /* precond == 4: largest metric block that is factorised (0 = default 3072) */
+    int tc_wait_polls;  /* polls of the bounded mbarrier wait for the tensor-core MMAs of the learned
+                           correction before it gives up with SPMPS_ERR_TIMEOUT (0 = default 2^24,
+                           about a second); after giving up the kernel still waits, with the default
+                           limit, for its MMAs in flight and frees its tensor memory */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -293,7 +307,9 @@ spmps_status spmps_profile(spmps_handle h, int enable);
  * algorithmic flops, same rule as spmps_apply_flops), 2 = the Davidson Ritz step (k_ritz),
  * 3 = the rest of each Davidson iteration outside the projected action (dots, gemv, residual,
  * Gram-Schmidt), 4 = the decimation eigen-solve and truncation, 5 = host time spent building and
- * uploading contraction plans (ms of host clock, launches = plans built).  Synchronises the
+ * uploading contraction plans (ms of host clock, launches = plans built), 6 = assembly and
+ * factorisation of the metric blocks (precond 4, once per two-site step), 7 = the per-iteration
+ * solves with them.  Synchronises the
  * handle's stream. */
 spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops);
 

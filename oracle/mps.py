@@ -33,7 +33,8 @@ from .mpo import rotate_mpo, identity_mpo
 from .quadrature import projector_quadrature
 
 LOCAL_Q = np.array([[0, 0], [1, -1], [1, 1], [2, 0]], dtype=np.int64)  # (n, 2m) of {0,b,a,ab}
-METRIC_SHIFT = 1e-10  # shift of the metric blocks in precond="metric_block" (|N_eff| <= 1)
+METRIC_SHIFT = 1e-7  # shift of the metric blocks in precond="metric_block" (|N_eff| <= 1)
+METRIC_FLOOR = 1e-14  # Ritz problem: n-eigenvalues below this are numerically zero
 
 
 def site_mask(ql, qr):
@@ -228,7 +229,7 @@ class Projected:
             out.append(np.where(mask, acc, 0.0))
         return tuple(out)
 
-    def metric_blocks(self, k):
+    def metric_blocks(self, k, max_dim=None):
         """The diagonal blocks of N_eff at sites (k, k+1) in the (N, M)-allowed entries of the
         two-site tensor, one block per (n of the left bond index, n(s1), n(s2)): a list of
         (positions in the flattened masked vector, dense block).  Block entries are
@@ -242,6 +243,8 @@ class Projected:
         out = []
         for kk in sorted(set(map(tuple, key))):
             pos = np.nonzero(np.all(key == kk, axis=1))[0]
+            if max_dim is not None and len(pos) > max_dim:
+                continue
             a, s1, s2, b = ia[pos], i1[pos], i2[pos], ib[pos]
             blk = np.zeros((len(pos), len(pos)))
             for g, cg in enumerate(self.c):
@@ -286,9 +289,10 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
     correction t = -r / (diag H - theta diag N), the denominator clamped to |.| >= clamp
     (precond="diag"), or t = cg_steps conjugate-gradient steps on N t = r from t = 0
     (precond="metric", an approximate N^+ r; needs ``apply_n``), or
-    t = (N_b + metric_shift I)^-1 r on every diagonal block N_b of N (precond="metric_block";
-    ``metric_blocks`` from Projected.metric_blocks: N is block-diagonal, so this is the inverse of
-    N shifted by metric_shift, which keeps directions of N-norm down to ~metric_shift);
+    t = (N_b + metric_shift I)^-1 r on every diagonal block N_b of N given in ``metric_blocks``
+    (precond="metric_block"; from Projected.metric_blocks: N is block-diagonal, so this is the
+    inverse of N shifted by metric_shift, which keeps directions of N-norm down to ~metric_shift;
+    entries of blocks left out keep the diagonal correction);
     restart from [x, previous x] when the basis reaches max_sub; converged when
     ||r|| < tol_r and |theta - theta_prev| < tol_theta."""
     shape = x0.shape
@@ -319,7 +323,8 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
         h = 0.5 * (h + h.T)
         n = 0.5 * (n + n.T)
         mu, Q = np.linalg.eigh(n)
-        keep = mu > eps_metric * mu.max()
+        # unit basis vectors and |N| <= 1: an n-eigenvalue below METRIC_FLOOR is numerically zero
+        keep = (mu > eps_metric * mu.max()) & (mu > METRIC_FLOOR)
         if mu.max() <= 0 or not keep.any():
             raise FloatingPointError("singular metric")
         X = Q[:, keep] / np.sqrt(mu[keep])
@@ -339,7 +344,9 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
         if precond == "metric":
             t = _cg_metric(lambda u: op_n(u), r, cg_steps)
         elif precond == "metric_block":
-            t = np.zeros_like(r)
+            den = dh - theta * dn
+            den = np.where(np.abs(den) < clamp, np.where(den < 0, -clamp, clamp), den)
+            t = -r / den
             for pos, blk in metric_blocks:
                 t[pos] = np.linalg.solve(blk + metric_shift * np.eye(len(pos)), r[pos])
         else:
@@ -372,6 +379,19 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
     full = np.zeros(sel.shape[0])
     full[sel] = x
     return DavidsonResult(theta, full.reshape(shape), max_iter, False, rn)
+
+
+def min_norm_representative(x, nx, metric_blocks, shift=METRIC_SHIFT):
+    """The two-site vector is defined only modulo ker N_eff (several results are correct); before
+    decimation the metric_block form takes the representative x' = (N + shift I)^-1 N x, built
+    from N x (masked, flattened) block by block: x' keeps every component of x along directions
+    of N-norm well above ``shift`` and drops the (near-)null ones, which P V x does not see but
+    which would otherwise dominate the singular values of x.  Entries of blocks left out of
+    ``metric_blocks`` keep x."""
+    out = np.array(x, dtype=float, copy=True)
+    for pos, blk in metric_blocks:
+        out[pos] = np.linalg.solve(blk + shift * np.eye(len(pos)), nx[pos])
+    return out
 
 
 def _cg_metric(apply_n, r, steps):
@@ -494,11 +514,20 @@ def two_site_step(P: Projected, k: int, move_right: bool, D: int, log: SweepLog,
     ql, qr = mps.labels[k], mps.labels[k + 2]
     mask = two_site_mask(ql, qr)
     dh, dn = P.diagonal(k)
+    blocks = None
     if dav.get("precond") == "metric_block":
-        dav = dict(dav, metric_blocks=P.metric_blocks(k))
+        blocks = P.metric_blocks(k, dav.pop("metric_max_dim", None))
+        dav = dict(dav, metric_blocks=blocks)
     res = davidson(lambda v: P.apply(v, k), x0, dh, dn, mask,
                    apply_n=lambda v: P.apply(v, k, which=("n",))[0], **dav)
-    Al, Ar, lm, disc = decimate(res.x, ql, qr, D, move_right)
+    x = res.x
+    if blocks is not None:
+        sel = mask.reshape(-1)
+        nx = P.apply(x, k, which=("n",))[0].reshape(-1)[sel]
+        full = np.zeros(mask.size)
+        full[sel] = min_norm_representative(x.reshape(-1)[sel], nx, blocks, dav.get("metric_shift", METRIC_SHIFT))
+        x = full.reshape(mask.shape)
+    Al, Ar, lm, disc = decimate(x, ql, qr, D, move_right)
     mps.A[k], mps.A[k + 1] = Al, Ar
     mps.labels[k + 1] = lm
     if move_right:

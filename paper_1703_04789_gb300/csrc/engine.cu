@@ -1357,6 +1357,8 @@ void spmps_default_options(spmps_options* o) {
     o->jacobi_smem_max = 0;
     o->precision = 0;
     o->autotune = 0;
+    o->metric_max_dim = 0;
+    o->tc_wait_polls = 0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1376,6 +1378,9 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     spmps_default_options(&o);
     if (opt) o = *opt;
     if (o.dav_max_sub < 4 || o.dav_max_sub > 32) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_sub must be in [4, 32]");
+    if (o.dav_max_iter < 1) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_iter must be >= 1");
+    if (o.metric_max_dim < 0 || o.tc_wait_polls < 0)
+        return fail(nullptr, SPMPS_ERR_BAD_INPUT, "metric_max_dim and tc_wait_polls must be >= 0");
     if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "jacobi_smem_max must be in [0, 112]");
     if (o.jacobi_smem_max == 0) o.jacobi_smem_max = 112;

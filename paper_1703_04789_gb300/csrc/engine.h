@@ -158,9 +158,9 @@ struct spmps_t {
     };
     bool profile = false;
     std::vector<TimerRec> timers_live, timers_free;
-    static constexpr int kProfKinds = 6;
-    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0};
-    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0};
+    static constexpr int kProfKinds = 8;
+    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace spmps {

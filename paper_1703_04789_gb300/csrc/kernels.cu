@@ -472,6 +472,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Incremental Ritz step (one CTA of 128 threads: one warp per SM sub-partition, so the FP64
 // products and the Jacobi sweeps use all four FP64 pipes of the SM).
+constexpr double kMetricFloor = 1e-14;
+
 __global__ void __launch_bounds__(128) k_ritz_inc(const double* __restrict__ h, const double* __restrict__ nm, int ldm,
                                                   int m, int reset, double eps, RitzState* __restrict__ st,
                                                   double* __restrict__ coef, double* __restrict__ scal) {
@@ -532,7 +534,9 @@ __global__ void __launch_bounds__(128) k_ritz_inc(const double* __restrict__ h, 
                 if (lane <= col) ny = fma(NS[lane * R + l], yl, ny);
             }
             const double nu2 = warp_sum(lane <= col ? y * ny : 0.0);
-            if (nu2 > eps * dmax && nu2 > 0.0) {
+            // the basis vectors have unit norm and |N_eff| <= 1: below kMetricFloor the metric is
+            // numerically zero (no state of the target spin is reachable), whatever eps says
+            if (nu2 > eps * dmax && nu2 > kMetricFloor) {
                 const double inv = 1.0 / sqrt(nu2);
                 X[lane + k * R] = lane <= col ? y * inv : 0.0;
                 __syncwarp();

@@ -199,7 +199,7 @@ spmps_status spmps_mlp_infer(spmps_handle h, const double* r, const double* dh, 
     if (tensor_cores) {
         CK(mlp::infer_tc(dr.as<double>(), dd.as<double>(), ddh.as<double>(), ddn.as<double>(), sc, sc + 2, sc + 7, n,
                          M.w2core.as<__nv_bfloat16>(), M.params.as<float>(), dout.as<double>(), M.err.as<int>(),
-                         h->stream));
+                         h->stream, h->opt.tc_wait_polls));
     } else {
         CK(dX.ensure(static_cast<size_t>(n) * mlp::N_FEATURES * sizeof(float)));
         CK(mlp::features(dr.as<double>(), dd.as<double>(), ddh.as<double>(), ddn.as<double>(), sc, sc + 2, sc + 7, n,

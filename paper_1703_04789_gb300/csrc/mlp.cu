@@ -250,6 +250,7 @@ __global__ void k_w2_core(const float* __restrict__ W2, __nv_bfloat16* __restric
         __float2bfloat16_rn(W2[e]);
 }
 
+constexpr int kWaitPolls = 1 << 24;  // default limit of the bounded mbarrier waits (about a second)
 constexpr size_t kInferSmem = static_cast<size_t>(kTileM) * HIDDEN * 2 + static_cast<size_t>(HIDDEN) * HIDDEN * 2 +
                               (N_FEATURES * HIDDEN + 3 * HIDDEN + 4) * sizeof(float) + 64;
 
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(128, 1) k_infer_tc(const double* __restrict__ 
                                                      const double* __restrict__ dd, int64_t n,
                                                      const __nv_bfloat16* __restrict__ w2core,
                                                      const float* __restrict__ params, double* __restrict__ out,
-                                                     int* __restrict__ err) {
+                                                     int* __restrict__ err, int wait_polls) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* As = smem;                                     // 128 x 256 bf16, 64 KB
     unsigned char* Bs = smem + kTileM * HIDDEN * 2;               // 256 x 256 bf16, 128 KB
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(128, 1) k_infer_tc(const double* __restrict__ 
     float* b3s = w3s + HIDDEN;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(b3s + 4);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    volatile uint32_t* wait_ok = tslot + 1;  // outcome of thread 0's bounded wait, read by every thread
     const int tid = threadIdx.x, warp = tid >> 5;
     // weights into shared memory
     {
@@ -347,15 +349,20 @@ __global__ void __launch_bounds__(128, 1) k_infer_tc(const double* __restrict__ 
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(mbar)));
         }
-        // bounded wait for the MMAs
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 24) && !done; ++it) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(smem_u32(mbar)), "r"(phase));
+        // bounded wait for the MMAs by thread 0; the outcome goes to every thread through shared
+        // memory, so the whole CTA takes the same path (the epilogue's loads are warp-collective)
+        if (tid == 0) {
+            uint32_t done = 0;
+            for (int it = 0; it < wait_polls && !done; ++it) {
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(smem_u32(mbar)), "r"(phase));
+            }
+            *wait_ok = done;
         }
-        if (!done) {
+        __syncthreads();
+        if (!*wait_ok) {
             failed = true;
             if (tid == 0) atomicExch(err, 1);
             break;
@@ -388,10 +395,11 @@ __global__ void __launch_bounds__(128, 1) k_infer_tc(const double* __restrict__ 
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
     }
-    if (failed) {
-        // give in-flight MMAs a further bounded wait before the tensor memory is released
+    if (failed && tid == 0) {
+        // give the in-flight MMAs a further bounded wait (the default limit) before the tensor
+        // memory is released
         uint32_t done = 0;
-        for (int it = 0; it < (1 << 24) && !done; ++it) {
+        for (int it = 0; it < kWaitPolls && !done; ++it) {
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                 : "=r"(done)
@@ -460,8 +468,9 @@ cudaError_t prepare_w2(const float* params, __nv_bfloat16* w2core, cudaStream_t 
 
 cudaError_t infer_tc(const double* r, const double* d, const double* dh, const double* dn, const double* theta,
                      const double* rr, const double* dd, int64_t n, const __nv_bfloat16* w2core, const float* params,
-                     double* out, int* err, cudaStream_t st) {
+                     double* out, int* err, cudaStream_t st, int wait_polls) {
     if (n <= 0) return cudaSuccess;
+    if (wait_polls <= 0) wait_polls = kWaitPolls;
     static int attr_device = -1;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -474,7 +483,7 @@ cudaError_t infer_tc(const double* r, const double* d, const double* dh, const d
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (n + kTileM - 1) / kTileM;
     const int grid = static_cast<int>(tiles < sms ? tiles : sms);
-    k_infer_tc<<<grid, 128, kInferSmem, st>>>(r, d, dh, dn, theta, rr, dd, n, w2core, params, out, err);
+    k_infer_tc<<<grid, 128, kInferSmem, st>>>(r, d, dh, dn, theta, rr, dd, n, w2core, params, out, err, wait_polls);
     return cudaGetLastError();
 }
 

@@ -40,10 +40,12 @@ cudaError_t targets(const double* xs, const double* xstar, const double* xdot, c
                     const int64_t* idx, int count, int n_iter, int64_t n, float* T, cudaStream_t st);
 cudaError_t prepare_w2(const float* params, __nv_bfloat16* w2core, cudaStream_t st);
 // out[i] = network(features of element i) with the 256 x 256 layer on tcgen05 (BF16 operands,
-// FP32 accumulation); err[0] is set when a bounded wait gave up.
+// FP32 accumulation); err[0] is set when the bounded wait for the MMAs gave up after wait_polls
+// polls (<= 0: the default of about a second); the kernel then waits once more with the default
+// limit for its MMAs in flight, frees its tensor memory and returns.
 cudaError_t infer_tc(const double* r, const double* d, const double* dh, const double* dn, const double* theta,
                      const double* rr, const double* dd, int64_t n, const __nv_bfloat16* w2core, const float* params,
-                     double* out, int* err, cudaStream_t st);
+                     double* out, int* err, cudaStream_t st, int wait_polls = 0);
 cudaError_t infer_f32(const float* X, int64_t n, const float* params, double* out, cudaStream_t st);
 // Forward + backward of the mean squared error on (X, T); writes grads (kParams) and *loss.
 cudaError_t train_step(TrainBuffers& b, const float* X, const float* T, int B, float* params, float* grads,

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "metric.h"
 
 using namespace spmps;
 using namespace spmps::eng;
@@ -46,6 +47,7 @@ int64_t x_size(spmps_t* h, int k) { return make_row_block_layout(h->bonds[k], h-
 // Device work buffers of the Davidson solver.
 struct DavBuffers {
     DevMem V, HV, NV, hm, nm, coef, coef_prev, scal, x, hx, nx, r, t, dh, dn, Q, tmp, cg_p, cg_ap, cg_res, dot, ritz;
+    MetricState metric;  // factors of the metric blocks (precond == 4)
 };
 
 spmps_status ensure_dav(spmps_t* h, DavBuffers& B, int64_t n, int ms) {
@@ -125,18 +127,35 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
                             double tol_theta, int cap, double switch_tol);
 
 spmps_status davidson(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out) {
+    B.metric.ok = false;
+    if (h->opt.precond == 4) {
+        // factors of the metric blocks for the correction (environments built first)
+        Plan* P = nullptr;
+        spmps_status st = get_apply_plan(h, k, &P);
+        if (st != SPMPS_OK) return st;
+        const int rec = h->profile ? prof_begin(h, h->stream, 6, 0.0) : -1;
+        st = metric_prepare(h, k, B.metric);
+        if (rec >= 0) prof_end(h, h->stream, rec);
+        if (st != SPMPS_OK) return st;
+    }
+    spmps_status st;
     if (h->opt.precision == 0) {
         h->apply_precision = 0;
-        return davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter, 0.0);
+        st = davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter, 0.0);
+    } else {
+        // reduced-precision H_eff x (tensor cores) until |r| < switch_tol, then the basis products
+        // are recomputed in FP64 and the same solve continues in FP64 to the final criteria
+        const double switch_tol = std::max(h->opt.precision == 1 ? 1e-3 : 1e-5, h->opt.dav_tol_r);
+        h->apply_precision = h->opt.precision;
+        st = davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter,
+                            switch_tol);
+        h->apply_precision = 0;
     }
-    // reduced-precision H_eff x (tensor cores) until |r| < switch_tol, then the basis products are
-    // recomputed in FP64 and the same solve continues in FP64 to the final criteria
-    const double switch_tol = std::max(h->opt.precision == 1 ? 1e-3 : 1e-5, h->opt.dav_tol_r);
-    h->apply_precision = h->opt.precision;
-    spmps_status st = davidson_stage(h, k, x0, B, out, h->opt.dav_tol_r, h->opt.dav_tol_theta, h->opt.dav_max_iter,
-                                     switch_tol);
-    h->apply_precision = 0;
-    return st;
+    if (st != SPMPS_OK || !B.metric.ok) return st;
+    // x is defined modulo ker N_eff: decimate the representative (N + s)^-1 N x (on the entries of
+    // the factorised blocks), which keeps the projected state and drops the (near-)null components
+    // that would otherwise dominate the singular values of x
+    return metric_solve(h, B.metric, B.nx.as<double>(), B.x.as<double>(), h->stream);
 }
 
 spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out, double tol_r,
@@ -250,6 +269,12 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         if (h->opt.precond == 1) {
             st = metric_cg(h, k, B, n, B.r.as<double>(), B.t.as<double>());
             if (st != SPMPS_OK) return st;
+        } else if (B.metric.ok) {
+            // t = (N_eff + s I)^-1 r through the factors of the metric blocks
+            const int mrec = h->profile ? prof_begin(h, h->stream, 7, 0.0) : -1;
+            st = metric_solve(h, B.metric, B.r.as<double>(), B.t.as<double>(), h->stream);
+            if (mrec >= 0) prof_end(h, h->stream, mrec);
+            if (st != SPMPS_OK) return st;
         } else if (h->opt.precond == 3) {
             // Olsen: t = M^-1 (-r + eps N x), eps such that x^T N t = 0, M = diag H - theta diag N:
             // t = t_diag + eps u, u = M^-1 N x, eps = -(Nx . t_diag) / (Nx . u)
@@ -281,7 +306,7 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
             CK(cudaMemsetAsync(ML.err.p, 0, sizeof(int), h->stream));
             CK(mlp::infer_tc(B.r.as<double>(), B.t.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, sc + 2,
                              sc + 7, n, ML.w2core.as<__nv_bfloat16>(), ML.params.as<float>(), B.cg_p.as<double>(),
-                             ML.err.as<int>(), h->stream));
+                             ML.err.as<int>(), h->stream, h->opt.tc_wait_polls));
             ++h->launches;
             tsrc = B.cg_p.as<double>();
         }

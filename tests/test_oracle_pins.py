@@ -481,7 +481,53 @@ def test_ordered_truncation_tie_rule():
     assert S.ordered_truncation(vals, tags, 10) == [0, 3, 2, 1, 4]  # 1e-9 < 1e-7 dropped
 
 
-@pytest.mark.parametrize("precond", ["diag", "metric"])
+@pytest.mark.parametrize("K,N,twoM,twoS,D,k", [(5, 5, 1, 1, 8, 1), (6, 6, 0, 0, 12, 2), (6, 6, 2, 2, 10, 3)])
+def test_metric_blocks_are_the_exact_diagonal_blocks_of_n_eff(K, N, twoM, twoS, D, k):
+    """N_eff, assembled column by column from the oracle's N network, vanishes between entries of
+    different (n(a), n(s1), n(s2)) and equals metric_blocks inside each block."""
+    labels, tens = inputs.random_mps(K, N, twoM, D, 7)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, Q.n_exact(K, N, twoM, twoS))
+    P.build_left(k)
+    mask = S.two_site_mask(P.mps.labels[k], P.mps.labels[k + 2])
+    sel = np.nonzero(mask.reshape(-1))[0]
+    Nm = np.zeros((len(sel), len(sel)))
+    for j, p in enumerate(sel):
+        e = np.zeros(mask.size); e[p] = 1.0
+        Nm[:, j] = P.apply(e.reshape(mask.shape), k, which=("n",))[0].reshape(-1)[sel]
+    blocks = P.metric_blocks(k)
+    covered = np.zeros_like(Nm, dtype=bool)
+    assert sorted(np.concatenate([pos for pos, _ in blocks]).tolist()) == list(range(len(sel)))
+    for pos, blk in blocks:
+        assert np.abs(Nm[np.ix_(pos, pos)] - blk).max() < 1e-14
+        covered[np.ix_(pos, pos)] = True
+    assert np.abs(Nm[~covered]).max() == 0.0
+    assert len(blocks) > 1
+
+
+def test_min_norm_representative_keeps_the_projected_state():
+    """x' = (N + shift)^-1 N x: N x' = N x up to the shift, x' has no component in ker N and
+    no larger norm than x (checked against a dense eigendecomposition of N)."""
+    K, N, twoM, twoS, D, k = 6, 6, 0, 0, 16, 2
+    labels, tens = inputs.random_mps(K, N, twoM, D, 3)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, Q.n_exact(K, N, twoM, twoS))
+    P.build_left(k)
+    mask = S.two_site_mask(P.mps.labels[k], P.mps.labels[k + 2])
+    sel = np.nonzero(mask.reshape(-1))[0]
+    blocks = P.metric_blocks(k)
+    Nm = np.zeros((len(sel), len(sel)))
+    for pos, blk in blocks:
+        Nm[np.ix_(pos, pos)] = blk
+    nu, V = np.linalg.eigh(Nm)
+    assert (nu < 1e-12).sum() > 0  # the two-site space of this bond has a null space
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(len(sel))
+    xp = S.min_norm_representative(x, Nm @ x, blocks, 1e-7)
+    assert np.abs(Nm @ xp - Nm @ x).max() < 1e-6 * np.abs(Nm @ x).max()
+    assert np.abs(V[:, nu < 1e-12].T @ xp).max() < 1e-8 * np.linalg.norm(x)
+    assert np.linalg.norm(xp) <= np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("precond", ["diag", "metric", "metric_block"])
 def test_davidson_matches_library_generalised_eigensolver(precond):
     """Special case that a library routine solves: random symmetric H, positive-definite N."""
     n = 60
@@ -491,7 +537,8 @@ def test_davidson_matches_library_generalised_eigensolver(precond):
     shape = (n,)
     ex = sla.eigh(H, Nm, eigvals_only=True)[0]
     res = S.davidson(lambda v: (H @ v, Nm @ v), rng.standard_normal(n), np.diag(H), np.diag(Nm),
-                     np.ones(shape, bool), tol_r=1e-9, precond=precond, apply_n=lambda v: Nm @ v)
+                     np.ones(shape, bool), tol_r=1e-9, precond=precond, apply_n=lambda v: Nm @ v,
+                     metric_blocks=[(np.arange(n), Nm)])
     assert res.converged
     assert abs(res.theta - ex) < 1e-10
     assert abs(res.x @ Nm @ res.x - 1.0) < 1e-10
