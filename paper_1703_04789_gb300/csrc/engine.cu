@@ -1384,7 +1384,7 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "jacobi_smem_max must be in [0, 112]");
     if (o.jacobi_smem_max == 0) o.jacobi_smem_max = 112;
-    if (o.precond < 0 || o.precond > 3) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precond must be 0, 1, 2 or 3");
+    if (o.precond < 0 || o.precond > 4) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precond must be 0, 1, 2, 3 or 4");
     if (o.precision < 0 || o.precision > 2) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "precision must be 0, 1 or 2");
     if (o.autotune != 0 && o.autotune != 1) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "autotune must be 0 or 1");
     int ndev = 0;

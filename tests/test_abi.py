@@ -43,6 +43,22 @@ def test_bad_inputs_rejected_without_device_work():
         with pytest.raises(SpmpsError) as ei:
             Spmps(*args)
         assert ei.value.status == 1, args
+    for kw in ({"dav_max_iter": 0}, {"dav_max_sub": 3}, {"metric_max_dim": -1}, {"tc_wait_polls": -2}):
+        with pytest.raises(SpmpsError) as ei:
+            Spmps(4, 4, 0, 0, 2, 8, **kw)
+        assert ei.value.status == 1, kw
+
+
+@pytest.mark.parametrize("precond", ["diag", "metric", "learned", "olsen", "metric_block"])
+def test_every_correction_option_passes_validation(precond):
+    """Valid options are never rejected as bad input (without a GPU the create call then stops at
+    the device with SPMPS_ERR_CUDA)."""
+    from paper_1703_04789_gb300 import Spmps, SpmpsError
+    library()
+    try:
+        Spmps(4, 4, 0, 0, 2, 8, precond=precond, metric_max_dim=64, tc_wait_polls=10).close()
+    except SpmpsError as e:
+        assert e.status != 1, e
 
 
 def test_no_silent_fallback_without_gpu():
