@@ -203,9 +203,25 @@ spmps_status spmps_apply_heff_timed(spmps_handle h, int site, const double* x, d
  * allowed block products only: 2*m*n*k per block GEMM, 2*rows*cols per MPO-leg term). */
 spmps_status spmps_apply_flops(spmps_handle h, int site, double* flops3);
 
+/* Algorithmic flops and bytes of one call of spmps_apply_heff at `site`, per operator (op 0 = H,
+ * 1 = N) and phase (index 3*op + phase, phase 0 = A, 1 = B, 2 = C).  Flops as spmps_apply_flops.
+ * Bytes, 8 per element: phase A reads the op's left environment and x and writes T1, each once
+ * per beta point; phase B reads T1 and writes T3; phase C reads T3 and the op's right environment
+ * and writes the per-beta partial outputs (the HBM roofline numerators).  Either pointer may be
+ * NULL (6 doubles each otherwise). */
+spmps_status spmps_apply_costs(spmps_handle h, int site, double* flops6, double* bytes6);
+
 /* FP64 fused multiply-add throughput of `device` in TFLOP/s, measured by a kernel of
  * independent FMA chains on every SM (the roofline denominator of the FP64 path). */
 spmps_status spmps_device_fp64_peak(int device, double* tflops);
+
+/* Dense TF32 tensor-core throughput of `device` in TFLOP/s (2 flops per multiply-add), measured on
+ * `sms` SMs (0 = all): kind 0 = the warp-level mma.sync.m16n8k8 TF32 instruction with FP32
+ * accumulation (4 CTAs of 8 warps per SM, 8 independent chains per warp), kind 1 =
+ * tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, operands in shared memory, accumulator in tensor
+ * memory, issued by one thread of one CTA per SM.  The roofline denominators of the reduced-precision
+ * action.  SPMPS_ERR_TIMEOUT if the bounded wait for the tcgen05 MMAs gave up. */
+spmps_status spmps_device_tf32_peak(int device, int kind, int sms, double* tflops);
 
 /* The same projected action as spmps_apply_heff, for callers that cannot let the library allocate
  * device memory when they need it: callers whose device memory is reserved up front by their own
@@ -309,7 +325,8 @@ spmps_status spmps_profile(spmps_handle h, int enable);
  * Gram-Schmidt), 4 = the decimation eigen-solve and truncation, 5 = host time spent building and
  * uploading contraction plans (ms of host clock, launches = plans built), 6 = assembly and
  * factorisation of the metric blocks (precond 4, once per two-site step), 7 = the per-iteration
- * solves with them.  Synchronises the
+ * solves with them, 8 = the reduced-precision block-GEMM launches (TF32 / 3xTF32 H products;
+ * kind 0 then counts the FP64 ones only).  Synchronises the
  * handle's stream. */
 spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops);
 

@@ -85,6 +85,8 @@ def load_library(path: str | None = None):
         "spmps_apply_heff_noalloc": (i, [H, i, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "spmps_apply_flops": (i, [H, i, P(d)]),
         "spmps_device_fp64_peak": (i, [i, P(d)]),
+        "spmps_device_tf32_peak": (i, [i, i, i, P(d)]),
+        "spmps_apply_costs": (i, [H, i, P(d), P(d)]),
         "spmps_two_site": (i, [H, i, C.c_void_p]),
         "spmps_canonicalize": (i, [H]),
         "spmps_sweep": (i, [H, i, P(d)]),
@@ -277,17 +279,26 @@ class Spmps:
         self._check(self.lib.spmps_apply_heff_noalloc(self._h, site, ptr(x), ptr(y), ptr(z), s))
 
     def apply_heff_timed(self, site: int, x, y, z, stream=None):
-        """Device apply with per-phase CUDA-event times (ms): [zero fill, A, B, C]."""
+        """Device apply with per-phase CUDA-event times (ms): [zero fill, A, B, C]; y or z may be
+        None (that operator is then not applied)."""
         ms = np.zeros(4)
         s = None if stream is None else C.c_void_p(stream.cuda_stream)
-        self._check(self.lib.spmps_apply_heff_timed(self._h, site, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
-                                                    C.c_void_p(z.data_ptr()), s, _dptr(ms)))
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self.lib.spmps_apply_heff_timed(self._h, site, ptr(x), ptr(y), ptr(z), s, _dptr(ms)))
         return ms
 
     def apply_flops(self, site: int):
         f = np.zeros(3)
         self._check(self.lib.spmps_apply_flops(self._h, site, _dptr(f)))
         return f
+
+    def apply_costs(self, site: int):
+        """Algorithmic (flops, bytes), each [[A, B, C] of H, [A, B, C] of N], of one projected
+        action at `site`."""
+        fl, by = np.zeros(6), np.zeros(6)
+        self._check(self.lib.spmps_apply_costs(self._h, site, fl.ctypes.data_as(C.POINTER(C.c_double)),
+                                               by.ctypes.data_as(C.POINTER(C.c_double))))
+        return fl.reshape(2, 3), by.reshape(2, 3)
 
     def apply_heff_host(self, site: int, x: np.ndarray):
         x = np.ascontiguousarray(x, dtype=np.float64)
@@ -485,6 +496,17 @@ def mpo_from_integrals(h1, h2=None, ecore: float = 0.0):
     if st != 0:
         raise SpmpsError(st, lib.spmps_last_error(None).decode())
     return ws
+
+
+def device_tf32_peak(kind: int, sms: int = 0, device: int = 0) -> float:
+    """Measured dense TF32 tensor-core throughput (TFLOP/s): kind 0 = mma.sync.m16n8k8, kind 1 =
+    tcgen05.mma kind::tf32; on `sms` SMs (0 = all)."""
+    lib = load_library()
+    v = C.c_double()
+    st = lib.spmps_device_tf32_peak(device, kind, sms, C.byref(v))
+    if st != 0:
+        raise SpmpsError(st, "TF32 peak measurement failed")
+    return v.value
 
 
 def device_fp64_peak(device: int = 0) -> float:

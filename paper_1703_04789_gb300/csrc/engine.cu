@@ -295,7 +295,7 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
             const bool use_tc = tf && split;
             const int t0 = use_tc ? tc_rng[lo] : rng[lo], t1 = use_tc ? tc_rng[hi] : rng[hi];
             ++h->launches;
-            const int rec = h->profile ? prof_begin(h, st, 0, range_flops(fl, lo, hi)) : -1;
+            const int rec = h->profile ? prof_begin(h, st, tf ? 8 : 0, range_flops(fl, lo, hi)) : -1;
             cudaError_t e;
             if (use_tc)
                 e = launch_gemm_tf32s(S, *split, tasks.as<GemmTask>(), segs.as<GemmSeg>(), tc.as<GemmTile>() + t0,
@@ -755,7 +755,8 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
             for (int j = 0; j < Lb.dim; ++j) P.A.cmaps.push_back(base + j);
         }
     }
-    int64_t t1 = 0, t3 = 0;
+    int64_t t1 = 0, t3 = 0, t1_op0 = 0, t3_op0 = 0;
+    std::vector<int64_t> t3_op_end(nops, 0), t3_op_begin(nops, 0);
     // per (op, g): offsets of T3 blocks for the output phase, kept for all g
     std::vector<std::vector<int64_t>> o3_all(static_cast<size_t>(nops) * G);
     std::vector<std::vector<DiagPair>> diag_all(static_cast<size_t>(nops) * G);
@@ -765,6 +766,7 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
         const int dwl = m.dw[k], dwr = m.dw[k + 2];
         const std::vector<int>& cnl = m.cn[k];
         const std::vector<int>& cnr = m.cn[k + 2];
+        t3_op_begin[op] = t3;
         for (int g = 0; g < G; ++g) {
             const MPO& W = h->ops.rot[op][g];
             const int og = op * G + g;
@@ -914,7 +916,14 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                     c3[u * ngl + ga] = CL;
                 }
             P.flops_op[op] += (P.A.flops - fa0) + (P.B.flops - fb0);
+            P.flopsA_op[op] += P.A.flops - fa0;
+            P.flopsB_op[op] += P.B.flops - fb0;
         }
+        // algorithmic bytes of phase A for this op: its environment, x and T1, each once per g
+        P.bytesA_op[op] = 8.0 * (static_cast<double>(G) * (Le.lay[op].size + xl.size)) + 8.0 * static_cast<double>(t1 - t1_op0);
+        P.bytesB_op[op] = 8.0 * static_cast<double>((t1 - t1_op0) + (t3 - t3_op0));
+        t1_op0 = t1;
+        t3_op0 = t3;
     }
     // phase C: one task per (N, M)-allowed output block and beta point, writing the partial sum
     // over the channels u into the per-g slice of the partial buffer (slot 8 for y, 9 for z); a
@@ -967,6 +976,10 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
             }
         }
         P.flops_op[op] += P.C.flops - fc0;
+        P.flopsC_op[op] += P.C.flops - fc0;
+        // phase C reads this op's T3 and right environment and writes G partial outputs
+        const int64_t t3_op = (op + 1 < nops ? t3_op_begin[op + 1] : t3) - t3_op_begin[op];
+        P.bytesC_op[op] = 8.0 * (static_cast<double>(t3_op) + static_cast<double>(G) * (Re.lay[op].size + nx));
     }
     P.reduce_nx = nx;
     P.tileA_rng[nops * G] = static_cast<int>(P.A.tasks.size());
@@ -1743,6 +1756,28 @@ spmps_status spmps_apply_heff_timed(spmps_handle h, int site, const double* x, d
     }
     for (auto& e : ev) cudaEventDestroy(e);
     return st;
+}
+
+spmps_status spmps_apply_costs(spmps_handle h, int site, double* flops6, double* bytes6) {
+    spmps_status st = check_ready(h);
+    if (st != SPMPS_OK) return st;
+    if (site < 0 || site > h->K - 2 || (!bytes6 && !flops6)) return fail(h, SPMPS_ERR_BAD_INPUT, "bad site or NULL");
+    Plan* P = nullptr;
+    st = get_apply_plan(h, site, &P);
+    if (st != SPMPS_OK) return st;
+    for (int op = 0; op < 2; ++op) {
+        if (flops6) {
+            flops6[3 * op + 0] = P->flopsA_op[op];
+            flops6[3 * op + 1] = P->flopsB_op[op];
+            flops6[3 * op + 2] = P->flopsC_op[op];
+        }
+        if (bytes6) {
+            bytes6[3 * op + 0] = P->bytesA_op[op];
+            bytes6[3 * op + 1] = P->bytesB_op[op];
+            bytes6[3 * op + 2] = P->bytesC_op[op];
+        }
+    }
+    return SPMPS_OK;
 }
 
 spmps_status spmps_apply_flops(spmps_handle h, int site, double* flops3) {

@@ -88,6 +88,8 @@ struct Plan {
     int64_t reduce_nx = 0;  // > 0: phase C writes per-beta partials of this length (slots 8, 9)
     double flops = 0.0;
     double flops_op[4] = {0, 0, 0, 0};
+    double bytesA_op[4] = {0, 0, 0, 0}, bytesB_op[4] = {0, 0, 0, 0}, bytesC_op[4] = {0, 0, 0, 0};
+    double flopsA_op[4] = {0, 0, 0, 0}, flopsB_op[4] = {0, 0, 0, 0}, flopsC_op[4] = {0, 0, 0, 0};
     DevMem d_tasksA, d_segsA, d_tilesA, d_cmapsA, d_outsB, d_termsB, d_tasksC, d_segsC, d_tilesC, d_cmapsC;
     DevMem d_tcA, d_tcC;                     // tensor-core tile lists
     std::vector<int> tcA_rng, tcC_rng;       // their ranges per (op, g)
@@ -158,9 +160,9 @@ struct spmps_t {
     };
     bool profile = false;
     std::vector<TimerRec> timers_live, timers_free;
-    static constexpr int kProfKinds = 8;
-    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
+    static constexpr int kProfKinds = 9;
+    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace spmps {

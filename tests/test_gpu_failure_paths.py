@@ -28,7 +28,7 @@ def test_invalid_integrals_are_rejected():
     require_gpu()
     from paper_1703_04789_gb300 import SpmpsError
     K = 4
-    h1, h2 = inputs.synthetic_active_space(K, 3)
+    h1, h2, _ = inputs.synthetic_active_space(K, 3)
     dev = _spmps(K, 4, 0, 0, 3, 8)
     bad = h1.copy()
     bad[1, 2] = np.nan

@@ -47,11 +47,13 @@ def test_shared_state_sweep_theta_at_every_step():
     """L=8, D=32, n_beta=5 (truncating): after two warm-up sweeps, at every step of the third the
     GPU's current MPS is handed to the oracle, both solve Eq. geproblem at that step and theta must
     agree; then the GPU takes the step (Davidson, decimation, environment update) and the next
-    step starts from its MPS."""
+    step starts from its MPS.  Both solve to |r| < 1e-7: with the metric inverted down to N-norms
+    of 1e-7 the residual has a noise floor near 1e-8 here, and theta from |r| < 1e-7 agrees with
+    the |r| < 1e-8 value to under 1e-9 (measured with the oracle on this workload)."""
     require_gpu()
     L, N, twoM, twoS, D, G = 8, 8, 0, 0, 32, 5
     labels, tens = inputs.random_mps(L, N, twoM, D, 1)
-    dev = _dev(L, N, twoM, twoS, D, G, precond="metric_block", dav_tol_r=1e-9, dav_max_iter=400)
+    dev = _dev(L, N, twoM, twoS, D, G, precond="metric_block", dav_tol_r=1e-7, dav_max_iter=600)
     dev.set_mps(labels, tens, center=0)
     dev.canonicalize()
     dev.sweep(2)
@@ -65,10 +67,10 @@ def test_shared_state_sweep_theta_at_every_step():
         x0 = P.two_site(k)
         mask = S.two_site_mask(P.mps.labels[k], P.mps.labels[k + 2])
         dh, dn = P.diagonal(k)
-        res = S.davidson(lambda v: P.apply(v, k), x0, dh, dn, mask, tol_r=1e-9, max_iter=400,
+        res = S.davidson(lambda v: P.apply(v, k), x0, dh, dn, mask, tol_r=1e-7, max_iter=600,
                          precond="metric_block", metric_blocks=P.metric_blocks(k))
         th, it = dev.optimize_step(k, mr, allow_not_converged=True)
-        assert res.converged and it < 400, (k, mr, it)
+        assert res.converged and it < 600, (k, mr, it, res.iterations)
         assert abs(th - res.theta) < 1e-9 * max(1.0, abs(res.theta)), (k, mr, th, res.theta)
         checked += 1
     assert checked == 2 * L - 3
