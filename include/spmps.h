@@ -92,7 +92,12 @@ typedef struct {
     int tc_wait_polls;  /* polls of the bounded mbarrier wait for the tensor-core MMAs of the learned
                            correction before it gives up with SPMPS_ERR_TIMEOUT (0 = default 2^24,
                            about a second); after giving up the kernel still waits, with the default
-                           limit, for its MMAs in flight and frees its tensor memory */
+                           limit, for its MMAs in flight and frees its tensor memory; the same
+                           limit applies to the stacked tcgen05 GEMM of the H products */
+    int tensor_core_kernel; /* precision 1 or 2: 0 = the stacked tcgen05 GEMM (kind::tf32, operands
+                           staged in shared memory, accumulator in tensor memory; tasks sharing
+                           their B operand stacked along M) (default), 1 = the warp-level
+                           mma.sync.m16n8k8 kernel on the same task lists */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */

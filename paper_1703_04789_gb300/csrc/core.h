@@ -120,7 +120,7 @@ struct GemmTask {
     int cmap;  // offset into the plan's column-map array, -1 for identity
     int M, N, ldc;
     int seg0, nseg;
-    int pad;
+    int key;   // tasks of one beta range with equal key share their B operand (tensor-core stacks)
 };
 struct GemmSeg {
     uint64_t a, b;

@@ -262,6 +262,26 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
     ranges(P.C.tiles, c_task_rng, P.tileC_rng);
     ranges(P.A.tc_tiles, a_task_rng, P.tcA_rng);
     ranges(P.C.tc_tiles, c_task_rng, P.tcC_rng);
+    // tcgen05 stacks of the H part (op 0) of an apply plan: phase A by ket label (x rows shared),
+    // phase C by right label (environment rows shared)
+    P.stA.clear();
+    P.stC.clear();
+    if (P.reduce_nx > 0 && static_cast<int>(a_task_rng.size()) > h->G && static_cast<int>(c_task_rng.size()) > h->G) {
+        const bool okA = build_tc_plan(P.A, a_task_rng, h->G, 128, P.stA);
+        const bool okC = build_tc_plan(P.C, c_task_rng, h->G, 64, P.stC);
+        if (okA && okC) {
+            for (TcPlan* T : {&P.stA, &P.stC}) {
+                DevMem* d = T == &P.stA ? P.d_stA : P.d_stC;
+                CK(upload(d[0], T->stacks, h->stream));
+                CK(upload(d[1], T->rows, h->stream));
+                CK(upload(d[2], T->segs, h->stream));
+                CK(upload(d[3], T->atab, h->stream));
+                CK(upload(d[4], T->units, h->stream));
+            }
+        } else {
+            P.stA.ok = P.stC.ok = false;
+        }
+    }
     CK(h->work1.ensure(std::max<int64_t>(1, P.t1_size) * sizeof(double)));
     CK(h->work2.ensure(std::max<int64_t>(1, P.t2_size) * sizeof(double)));
     CK(cudaStreamSynchronize(h->stream));
@@ -292,6 +312,24 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
                     const std::vector<int>& tc_rng, int a, int b) -> cudaError_t {
         auto one = [&](int lo, int hi, int tf) -> cudaError_t {
             if (hi <= lo) return cudaSuccess;
+            const TcPlan& TP = &tasks == &P.d_tasksA ? P.stA : P.stC;
+            if (tf && split && TP.ok && h->opt.tensor_core_kernel == 0 && hi <= G) {
+                // stacked tcgen05 GEMM over the units of the H-part ranges [lo, hi)
+                const DevMem* d = &tasks == &P.d_tasksA ? P.d_stA : P.d_stC;
+                ++h->launches;
+                const int rec = h->profile ? prof_begin(h, st, 8, range_flops(fl, lo, hi)) : -1;
+                cudaError_t e2 = cudaSuccess;
+                if (!h->tc_err.p) {
+                    e2 = h->tc_err.ensure(sizeof(int));
+                    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), st);
+                }
+                if (e2 == cudaSuccess)
+                    e2 = launch_gemm_tc(S, *split, d[0].as<TcStack>(), d[1].as<TcRow>(), d[2].as<TcSeg>(),
+                                        d[3].as<uint64_t>(), cmaps.as<int>(), d[4].as<int4>(), TP.unit_rng[lo],
+                                        TP.unit_rng[hi], TP.nt, tf == 2, h->tc_err.as<int>(), h->opt.tc_wait_polls, st);
+                if (rec >= 0) prof_end(h, st, rec);
+                return e2;
+            }
             const bool use_tc = tf && split;
             const int t0 = use_tc ? tc_rng[lo] : rng[lo], t1 = use_tc ? tc_rng[hi] : rng[hi];
             ++h->launches;
@@ -854,6 +892,7 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                         T.cmap = cmap_off[l];
                         T.M = M;
                         T.N = xl.width[l];
+                        T.key = static_cast<int>(l);  // all products of one ket label read x[l]
                         T.ldc = CL.width;
                         T.seg0 = static_cast<int>(P.A.segs.size());
                         T.nseg = 1;
@@ -949,6 +988,7 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                     T.cmap = -1;
                     T.M = La.dim;
                     T.N = Lb.dim;
+                    T.key = lb;  // all output blocks of one right label read its environment rows
                     T.ldc = xl.width[la];
                     T.seg0 = static_cast<int>(P.C.segs.size());
                     for (int u = 0; u < dwr; ++u) {
@@ -1372,6 +1412,7 @@ void spmps_default_options(spmps_options* o) {
     o->autotune = 0;
     o->metric_max_dim = 0;
     o->tc_wait_polls = 0;
+    o->tensor_core_kernel = 0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1392,6 +1433,8 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (opt) o = *opt;
     if (o.dav_max_sub < 4 || o.dav_max_sub > 32) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_sub must be in [4, 32]");
     if (o.dav_max_iter < 1) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_iter must be >= 1");
+    if (o.tensor_core_kernel < 0 || o.tensor_core_kernel > 1)
+        return fail(nullptr, SPMPS_ERR_BAD_INPUT, "tensor_core_kernel must be 0 or 1");
     if (o.metric_max_dim < 0 || o.tc_wait_polls < 0)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "metric_max_dim and tc_wait_polls must be >= 0");
     if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)

@@ -12,6 +12,7 @@
 #include "core.h"
 #include "kernels.h"
 #include "mlp.h"
+#include "tc_gemm.h"
 
 namespace spmps {
 
@@ -93,6 +94,8 @@ struct Plan {
     DevMem d_tasksA, d_segsA, d_tilesA, d_cmapsA, d_outsB, d_termsB, d_tasksC, d_segsC, d_tilesC, d_cmapsC;
     DevMem d_tcA, d_tcC;                     // tensor-core tile lists
     std::vector<int> tcA_rng, tcC_rng;       // their ranges per (op, g)
+    TcPlan stA, stC;                         // tcgen05 stacks of the H part, phases A and C
+    DevMem d_stA[5], d_stC[5];               // their stacks, rows, segments, A table, units
     // diagonal (apply plans only)
     std::vector<DiagBlock> diag_blocks;
     std::vector<DiagTerm> diag_terms;
@@ -128,6 +131,7 @@ struct spmps_t {
     cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
     // orders a caller's stream after the handle's stream in spmps_apply_heff_noalloc
     cudaEvent_t noalloc_order = nullptr;
+    spmps::DevMem tc_err;  // set by the stacked tensor-core GEMM when a bounded wait gave up
     std::vector<double> beta, cg;
 
     bool has_ham = false, has_mps = false;

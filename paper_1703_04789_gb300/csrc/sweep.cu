@@ -348,11 +348,13 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         if (rec >= 0) prof_end(h, h->stream, rec);
         // one host read per iteration: theta, kept metric directions, |r|^2, |t|^2
         CK(cudaMemcpyAsync(host, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        int infer_err = 0;
+        int infer_err = 0, tc_err = 0;
         if (learned) CK(cudaMemcpyAsync(&infer_err, ML.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        if (h->tc_err.p) CK(cudaMemcpyAsync(&tc_err, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         ++h->dav_iters;
         if (infer_err) return fail(h, SPMPS_ERR_TIMEOUT, "learned correction: a bounded tensor-core wait gave up");
+        if (tc_err) return fail(h, SPMPS_ERR_TIMEOUT, "tensor-core block GEMM: a bounded wait gave up");
         if (host[1] < 0.5) return fail(h, SPMPS_ERR_SINGULAR_METRIC, "projected metric has no usable direction");
         if (!std::isfinite(host[0]) || !std::isfinite(host[2])) return fail(h, SPMPS_ERR_NAN, "non-finite Ritz value");
         const double theta = host[0], rn = std::sqrt(std::max(host[2], 0.0));

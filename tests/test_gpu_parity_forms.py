@@ -49,7 +49,8 @@ def _max_label(q):
 def test_reduced_precision_action_matches_oracle_full_size(twoM, twoS):
     """Hubbard L=24, half filling, D=256, n_beta=8, middle site, with the fast form's settings
     (autotuned tiles, pre-split tensor-core operands): sampled bra rows of y against the oracle
-    within the split bound, z at FP64 accuracy, for TF32 and 3xTF32."""
+    within the split bound, z at FP64 accuracy, for TF32 and 3xTF32 on the stacked tcgen05 GEMM and
+    for 3xTF32 on the warp-level mma.sync kernel."""
     require_gpu()
     from paper_1703_04789_gb300 import Spmps
     L, N, D, G, U = 24, 24, 256, 8, 4.0
@@ -66,8 +67,10 @@ def test_reduced_precision_action_matches_oracle_full_size(twoM, twoS):
     mask = S.two_site_mask(ql, qr)[rows]
     K_A = _max_label(ql)
     K_C = 6 * _max_group(qr)
-    for prec, u in (("3xtf32", 4 * 2.0 ** -22), ("tf32", 2 * 2.0 ** -11 + 2.0 ** -21)):
-        dev = Spmps(L, N, twoM, twoS, G, D, precision=prec, autotune=True)
+    cases = [("3xtf32", 4 * 2.0 ** -22, "tcgen05"), ("tf32", 2 * 2.0 ** -11 + 2.0 ** -21, "tcgen05"),
+             ("3xtf32", 4 * 2.0 ** -22, "mma_sync")]
+    for prec, u, kern in cases:
+        dev = Spmps(L, N, twoM, twoS, G, D, precision=prec, autotune=True, tensor_core_kernel=kern)
         dev.set_hubbard(1.0, U)
         dev.set_mps(P.mps.labels, P.mps.A, center=0)
         lay = dev.x_layout(k)
@@ -78,7 +81,7 @@ def test_reduced_precision_action_matches_oracle_full_size(twoM, twoS):
         gA, gC = u + K_A * 2.0 ** -24, u + K_C * 2.0 ** -24
         bound = (gA + gC + gA * gC) * y_abs
         err = np.abs(y - y_ref)
-        assert np.all(err[mask] <= bound[mask] + 1e-300), (prec, float((err / np.maximum(bound, 1e-300))[mask].max()))
+        assert np.all(err[mask] <= bound[mask] + 1e-300), (prec, kern, float((err / np.maximum(bound, 1e-300))[mask].max()))
         assert err[mask].max() > 0.0  # the tensor-core path ran
         assert np.abs(z - z_ref).max() <= 1e-10 * max(1.0, np.abs(z_ref).max())
 
