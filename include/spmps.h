@@ -98,6 +98,13 @@ typedef struct {
                            staged in shared memory, accumulator in tensor memory; tasks sharing
                            their B operand stacked along M) (default), 1 = the warp-level
                            mma.sync.m16n8k8 kernel on the same task lists */
+    double m_screen;    /* approximate M-sector screening (Sec. 2.3.1, closing paragraph), 0 = off
+                           (default): per operator, beta point and MPO channel, the block products
+                           whose environment sub-block between a bra label and a ket label (M mixed
+                           by the rotation) has a Frobenius norm below m_screen times the largest
+                           such sub-block of the channel are dropped from phases A and C.  An
+                           approximation: y and z change by amounts of the order of m_screen;
+                           spmps_apply_flops reports the reduced work. */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -221,8 +228,8 @@ spmps_status spmps_apply_costs(spmps_handle h, int site, double* flops6, double*
 spmps_status spmps_device_fp64_peak(int device, double* tflops);
 
 /* Dense TF32 tensor-core throughput of `device` in TFLOP/s (2 flops per multiply-add), measured on
- * `sms` SMs (0 = all): kind 0 = the warp-level mma.sync.m16n8k8 TF32 instruction with FP32
- * accumulation (4 CTAs of 8 warps per SM, 8 independent chains per warp), kind 1 =
+ * `sms` SMs (0 = all), one CTA per SM: kind 0 = the warp-level mma.sync.m16n8k8 TF32 instruction
+ * with FP32 accumulation (32 warps, 8 independent chains per warp), kind 1 =
  * tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, operands in shared memory, accumulator in tensor
  * memory, issued by one thread of one CTA per SM.  The roofline denominators of the reduced-precision
  * action.  SPMPS_ERR_TIMEOUT if the bounded wait for the tcgen05 MMAs gave up. */

@@ -119,6 +119,24 @@ def right_env_update(R, A, W):
     return np.einsum("asb,cswb->awc", A, T)
 
 
+def screen_environment(E, q_bra, q_ket, tau):
+    """Approximate M-sector screening (Sec. 2.3.1, closing paragraph: for a state near the target
+    spin the rotation introduces few states in the other M sectors).  For every channel w of the
+    environment E[a, w, a'] (bra index a, ket index a'), the sub-blocks (label(a), label(a')) whose
+    Frobenius norm is below tau times the largest sub-block norm of that channel are set to zero."""
+    out = E.copy()
+    lb = [np.nonzero(np.all(q_bra == q, axis=1))[0] for q in np.unique(q_bra, axis=0)]
+    lk = [np.nonzero(np.all(q_ket == q, axis=1))[0] for q in np.unique(q_ket, axis=0)]
+    for w in range(E.shape[1]):
+        norms = np.array([[np.linalg.norm(E[np.ix_(a, [w], c)]) for c in lk] for a in lb])
+        cut = tau * norms.max() if norms.size else 0.0
+        for i, a in enumerate(lb):
+            for j, c in enumerate(lk):
+                if norms[i, j] < cut:
+                    out[np.ix_(a, [w], c)] = 0.0
+    return out
+
+
 class Projected:
     """Per-beta environments of H exp(-i b_g S_y) and of exp(-i b_g S_y) for one MPS."""
 
@@ -164,8 +182,10 @@ class Projected:
 
     # ---- the projected action -------------------------------------------------------------
 
-    def apply(self, x, k, which=("h", "n")):
-        """(y, z) = (H_eff x, N_eff x) at sites (k, k+1); x has shape (Dl, 4, 4, Dr)."""
+    def apply(self, x, k, which=("h", "n"), screen=0.0):
+        """(y, z) = (H_eff x, N_eff x) at sites (k, k+1); x has shape (Dl, 4, 4, Dr).  With
+        screen > 0 the environments are first screened (``screen_environment``): the M-sector
+        screening of Sec. 2.3.1's closing paragraph, an approximation."""
         ql, qr = self.mps.labels[k], self.mps.labels[k + 2]
         mask = two_site_mask(ql, qr)
         out = []
@@ -178,6 +198,9 @@ class Projected:
                 else:
                     L, R = self.Ln[g][k], self.Rn[g][k + 2]
                     W1, W2 = self.Wn[g][k], self.Wn[g][k + 1]
+                if screen > 0.0:
+                    L = screen_environment(L, ql, ql, screen)
+                    R = screen_environment(R, qr, qr, screen)
                 T = np.einsum("awc,ctid->awtid", L, x)
                 T = np.einsum("awtid,wvst->avsid", T, W1)
                 T = np.einsum("avsid,vuji->asjud", T, W2)

@@ -766,7 +766,9 @@ struct DiagPair {
 
 // ---- the projected action plan ---------------------------------------------------------------
 // Slots: 0 = x, 1 = y, 2 = z, 3 = T1, 4 = T3, 5 = L(bond k), 6 = R(bond k+2).
-void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re, Plan& P) {
+void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re, Plan& P, const EnvNorms* nL,
+                      const EnvNorms* nR, double tau) {
+    const bool screen = tau > 0.0 && nL && nR;
     const Bond& bl = h->bonds[k];
     const Bond& br = h->bonds[k + 2];
     const RowBlockLayout xl = make_row_block_layout(bl, br, 16);
@@ -884,29 +886,39 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                     if (CL.width == 0) continue;
                     const int M = bl.groups[ga].dim;
                     o1[w * ngl + ga] = t1;
+                    const Group& Ga = bl.groups[ga];
                     for (int l = bl.groups[gap].first; l < bl.groups[gap].first + bl.groups[gap].count; ++l) {
                         if (xl.width[l] == 0) continue;
                         const Label& Ll = bl.labels[l];
-                        GemmTask T{};
-                        T.c = handle(3, t1);
-                        T.cmap = cmap_off[l];
-                        T.M = M;
-                        T.N = xl.width[l];
-                        T.key = static_cast<int>(l);  // all products of one ket label read x[l]
-                        T.ldc = CL.width;
-                        T.seg0 = static_cast<int>(P.A.segs.size());
-                        T.nseg = 1;
-                        GemmSeg sg{};
-                        sg.a = handle(5, Le.base[og] + loff + (Ll.off - bl.groups[gap].off));
-                        sg.a_rs = bl.groups[gap].dim;
-                        sg.a_cs = 1;
-                        sg.K = Ll.dim;
-                        sg.b = handle(0, xl.row_off[l]);
-                        sg.b_rs = xl.width[l];
-                        sg.b_cs = 1;
-                                                P.A.segs.push_back(sg);
-                        P.A.tasks.push_back(T);
-                        P.A.flops += 2.0 * T.M * T.N * sg.K;
+                        // unscreened: one task over all bra rows of the group; screened: one task per
+                        // bra label, dropped when its environment sub-block is below the threshold
+                        const int nsub = screen ? Ga.count : 1;
+                        for (int q = 0; q < nsub; ++q) {
+                            const int row0 = screen ? bl.labels[Ga.first + q].off - Ga.off : 0;
+                            const int rows = screen ? bl.labels[Ga.first + q].dim : M;
+                            if (screen && nL->dropped(op, g, w, ga, q, l - bl.groups[gap].first, tau)) continue;
+                            GemmTask T{};
+                            T.c = handle(3, t1 + static_cast<int64_t>(row0) * CL.width);
+                            T.cmap = cmap_off[l];
+                            T.M = rows;
+                            T.N = xl.width[l];
+                            T.key = static_cast<int>(l);  // all products of one ket label read x[l]
+                            T.ldc = CL.width;
+                            T.seg0 = static_cast<int>(P.A.segs.size());
+                            T.nseg = 1;
+                            GemmSeg sg{};
+                            sg.a = handle(5, Le.base[og] + loff + static_cast<int64_t>(row0) * bl.groups[gap].dim +
+                                                 (Ll.off - bl.groups[gap].off));
+                            sg.a_rs = bl.groups[gap].dim;
+                            sg.a_cs = 1;
+                            sg.K = Ll.dim;
+                            sg.b = handle(0, xl.row_off[l]);
+                            sg.b_rs = xl.width[l];
+                            sg.b_cs = 1;
+                            P.A.segs.push_back(sg);
+                            P.A.tasks.push_back(T);
+                            P.A.flops += 2.0 * T.M * T.N * sg.K;
+                        }
                     }
                     t1 += static_cast<int64_t>(M) * CL.width;
                     c1[w * ngl + ga] = CL;
@@ -998,17 +1010,28 @@ void build_apply_plan(spmps_t* h, int k, const EnvStore& Le, const EnvStore& Re,
                         if (C3.col[s] < 0) continue;
                         const int64_t roff = Re.lay[op].off[u * ngr + gb];
                         if (roff < 0) continue;
-                        const int K = br.groups[C3.group[s]].dim;
-                        GemmSeg sg{};
-                        sg.a = handle(4, s3 + static_cast<int64_t>(La.off - bl.groups[ga].off) * C3.width + C3.col[s]);
-                        sg.a_rs = C3.width;
-                        sg.a_cs = 1;
-                        sg.K = K;
-                        sg.b = handle(6, Re.base[og] + roff + static_cast<int64_t>(Lb.off - br.groups[gb].off) * K);
-                        sg.b_rs = 1;
-                        sg.b_cs = K;
-                        P.C.segs.push_back(sg);
-                        P.C.flops += 2.0 * T.M * T.N * K;
+                        const Group& Gk = br.groups[C3.group[s]];
+                        const int K = Gk.dim;
+                        // unscreened: one segment over the ket group; screened: one per ket label,
+                        // dropped when its environment sub-block is below the threshold
+                        const int nsub = screen ? Gk.count : 1;
+                        for (int q = 0; q < nsub; ++q) {
+                            const int k0 = screen ? br.labels[Gk.first + q].off - Gk.off : 0;
+                            const int kl = screen ? br.labels[Gk.first + q].dim : K;
+                            if (screen && nR->dropped(op, g, u, gb, lb - br.groups[gb].first, q, tau))
+                                continue;
+                            GemmSeg sg{};
+                            sg.a = handle(4, s3 + static_cast<int64_t>(La.off - bl.groups[ga].off) * C3.width + C3.col[s] +
+                                                 k0);
+                            sg.a_rs = C3.width;
+                            sg.a_cs = 1;
+                            sg.K = kl;
+                            sg.b = handle(6, Re.base[og] + roff + static_cast<int64_t>(Lb.off - br.groups[gb].off) * K + k0);
+                            sg.b_rs = 1;
+                            sg.b_cs = K;
+                            P.C.segs.push_back(sg);
+                            P.C.flops += 2.0 * T.M * T.N * kl;
+                        }
                     }
                     T.nseg = static_cast<int>(P.C.segs.size()) - T.seg0;
                     P.C.tasks.push_back(T);
@@ -1240,9 +1263,22 @@ spmps_status tune_apply_plan(spmps_t* h, int k, Plan& P) {
 spmps_status get_apply_plan(spmps_t* h, int k, Plan** out) {
     spmps_status st = ensure_envs(h, k);
     if (st != SPMPS_OK) return st;
+    const double tau = h->opt.m_screen;
+    if (tau > 0.0 && h->apply_plans[k] &&
+        (h->apply_plans[k]->envL_version != h->Lenv[k].version || h->apply_plans[k]->envR_version != h->Renv[k + 2].version))
+        h->apply_plans[k].reset();  // screened plans follow the environment values
     if (!h->apply_plans[k]) {
         auto P = std::make_unique<Plan>();
-        build_apply_plan(h, k, h->Lenv[k], h->Renv[k + 2], *P);
+        EnvNorms nL, nR;
+        if (tau > 0.0) {
+            st = env_subblock_norms(h, h->Lenv[k], h->bonds[k], k, nL);
+            if (st != SPMPS_OK) return st;
+            st = env_subblock_norms(h, h->Renv[k + 2], h->bonds[k + 2], k + 2, nR);
+            if (st != SPMPS_OK) return st;
+        }
+        build_apply_plan(h, k, h->Lenv[k], h->Renv[k + 2], *P, &nL, &nR, tau);
+        P->envL_version = h->Lenv[k].version;
+        P->envR_version = h->Renv[k + 2].version;
         {
             int64_t sz[kMaxSlots];
             for (auto& v : sz) v = -1;
@@ -1413,6 +1449,7 @@ void spmps_default_options(spmps_options* o) {
     o->metric_max_dim = 0;
     o->tc_wait_polls = 0;
     o->tensor_core_kernel = 0;
+    o->m_screen = 0.0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1433,6 +1470,7 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (opt) o = *opt;
     if (o.dav_max_sub < 4 || o.dav_max_sub > 32) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_sub must be in [4, 32]");
     if (o.dav_max_iter < 1) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "dav_max_iter must be >= 1");
+    if (!(o.m_screen >= 0.0 && o.m_screen < 1.0)) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "m_screen must be in [0, 1)");
     if (o.tensor_core_kernel < 0 || o.tensor_core_kernel > 1)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "tensor_core_kernel must be 0 or 1");
     if (o.metric_max_dim < 0 || o.tc_wait_polls < 0)

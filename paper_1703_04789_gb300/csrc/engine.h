@@ -74,6 +74,26 @@ struct EnvStore {
     uint64_t split_version = 0;    // version of buf that split was made from (0: none)
 };
 
+// Frobenius norms of the (bra label, ket label) sub-blocks of one bond's environments, per
+// operator, beta point and channel (the approximate M-sector screening).
+struct EnvNorms {
+    int ngroups = 0;
+    std::vector<int> dw, wbase;   // per op: channels, first (g, w) slot
+    std::vector<double> wmax;     // per (op, g, w) slot: largest sub-block norm of the channel
+    std::vector<int64_t> start;   // per (slot, bra group): first norm, -1 if the block is absent
+    std::vector<int> ncols;       // per (slot, bra group): labels of the ket group
+    std::vector<double> norms;
+    int slot(int op, int g, int w) const { return wbase[op] + g * dw[op] + w; }
+    // below tau * (largest norm of the channel): the block product is dropped
+    bool dropped(int op, int g, int w, int ga, int la_local, int lp_local, double tau) const {
+        const int sl = slot(op, g, w);
+        const int64_t st = start[static_cast<int64_t>(sl) * ngroups + ga];
+        if (st < 0) return true;
+        return norms[st + static_cast<int64_t>(la_local) * ncols[static_cast<int64_t>(sl) * ngroups + ga] + lp_local] <
+               tau * wmax[sl];
+    }
+};
+
 // A three-phase contraction plan (GEMM, MPO-leg combination, GEMM), uploaded to the device.
 struct Plan {
     GemmPlan A, C;
@@ -101,6 +121,8 @@ struct Plan {
     std::vector<DiagTerm> diag_terms;
     DevMem d_diag_blocks, d_diag_terms;
     bool ready = false;
+    // environment versions the plan was built for (screened plans depend on their values)
+    uint64_t envL_version = 0, envR_version = 0;
 };
 
 }  // namespace spmps
@@ -188,6 +210,7 @@ spmps_status plan_upload(spmps_t* h, Plan& P);
 spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t st, cudaEvent_t* ev = nullptr,
                       const SlotsF* split = nullptr);
 spmps_status update_left(spmps_t* h, int i);
+spmps_status env_subblock_norms(spmps_t* h, const EnvStore& E, const Bond& b, int bond, EnvNorms& out);
 spmps_status update_right(spmps_t* h, int i);
 spmps_status ensure_envs(spmps_t* h, int k);
 void invalidate_all(spmps_t* h);

@@ -15,7 +15,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 }
 
 // Independent accumulator chains per warp: 8 m16n8k8 MMAs in flight per loop step.
-__global__ void __launch_bounds__(256) k_mma_sync_tf32_peak(int iters, float* out) {
+__global__ void __launch_bounds__(1024) k_mma_sync_tf32_peak(int iters, float* out) {
     uint32_t a[4], b[2];
     for (int q = 0; q < 4; ++q) a[q] = __float_as_uint(1e-3f * (threadIdx.x + q));
     for (int q = 0; q < 2; ++q) b[q] = __float_as_uint(1e-3f * (threadIdx.x - q));
@@ -142,12 +142,12 @@ extern "C" spmps_status spmps_device_tf32_peak(int device, int kind, int sms, do
     float ms = 0.0f;
     cudaError_t e = cudaSuccess;
     if (kind == 0) {
-        const int threads = 256, iters = 1 << 14;
-        k_mma_sync_tf32_peak<<<blocks * 4, threads>>>(64, out);
+        const int threads = 1024, iters = 1 << 13;  // one CTA of 32 warps per SM
+        k_mma_sync_tf32_peak<<<blocks, threads>>>(64, out);
         cudaEventRecord(e0);
-        k_mma_sync_tf32_peak<<<blocks * 4, threads>>>(iters, out);
+        k_mma_sync_tf32_peak<<<blocks, threads>>>(iters, out);
         cudaEventRecord(e1);
-        flops = 2.0 * 16 * 8 * 8 * 8.0 * iters * (threads / 32) * static_cast<double>(blocks * 4);
+        flops = 2.0 * 16 * 8 * 8 * 8.0 * iters * (threads / 32) * static_cast<double>(blocks);
     } else {
         const int iters = 1 << 12;
         e = cudaFuncSetAttribute(k_tcgen05_tf32_peak, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem);

@@ -83,6 +83,10 @@ constexpr int kTileK = 32;                        // K per shared-memory stage (
 constexpr int kTileBytesA = kTileM * kTileK * 4;  // one TF32 plane of A
 constexpr int kMaxNt = 128;
 constexpr int kDefaultWaitPolls = 1 << 24;
+constexpr int kCtrlBytes = 1024;  // mbarrier, tensor-memory address and flags, padded to the tile alignment
+constexpr int kTileBytes = 2 * kTileBytesA + 2 * kMaxNt * kTileK * 4;
+constexpr int kStageBytes = kTileM * (kMaxNt + 1) * 4;  // FP32 output stage (padded rows)
+constexpr size_t kSmemBytes = kCtrlBytes + (kTileBytes > kStageBytes ? kTileBytes : kStageBytes);
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -125,12 +129,14 @@ __global__ void __launch_bounds__(128, 3) k_gemm_tc(Slots S, SlotsF F, const TcS
                                                    const int4* __restrict__ units, int u0, int nt,
                                                    int* __restrict__ err, int wait_polls) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* Ahi = smem;
-    unsigned char* Alo = smem + kTileBytesA;
-    unsigned char* Bhi = smem + 2 * kTileBytesA;
-    unsigned char* Blo = Bhi + kMaxNt * kTileK * 4;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + kMaxNt * kTileK * 4);
+    // control words first, then the operand tiles (1024-aligned); after the K loop the tiles'
+    // space holds the FP32 output stage of the epilogue
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    unsigned char* Ahi = smem + kCtrlBytes;
+    unsigned char* Alo = Ahi + kTileBytesA;
+    unsigned char* Bhi = Alo + kTileBytesA;
+    unsigned char* Blo = Bhi + kMaxNt * kTileK * 4;
     volatile uint32_t* flag = tslot + 1;    // outcome of thread 0's bounded wait
     volatile uint32_t* issued = tslot + 2;  // whether any MMA wrote the accumulator
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -225,15 +231,11 @@ __global__ void __launch_bounds__(128, 3) k_gemm_tc(Slots S, SlotsF F, const TcS
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!failed) {
-        // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 (stacked rows m0 + 32w + lane)
-        const int r = m0 + warp * 32 + lane;
-        const bool ok_row = r < st.nrows;
-        double* C = nullptr;
-        if (ok_row) {
-            const uint64_t c = rows[st.row0 + r].c;
-            C = S.p[c >> 56] + static_cast<int64_t>(c & 0x00FFFFFFFFFFFFFFull);
-        }
-        const int* cm = st.cmap >= 0 ? cmaps + st.cmap : nullptr;
+        // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 (tile rows) into a shared-memory stage
+        // (the operand buffers are free now), then every warp writes whole rows with its lanes
+        // along the columns, so the stores of a row are contiguous
+        float* stage = reinterpret_cast<float*>(smem + kCtrlBytes);
+        const int ld = nt + 1;
         const bool any = *issued != 0;
         for (int cb = 0; cb < nt; cb += 32) {
             uint32_t v[32];
@@ -248,12 +250,20 @@ __global__ void __launch_bounds__(128, 3) k_gemm_tc(Slots S, SlotsF F, const TcS
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (ok_row) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int n = n0 + cb + q;
-                    if (n < st.N && cb + q < nt) C[cm ? cm[n] : n] = any ? static_cast<double>(__uint_as_float(v[q])) : 0.0;
-                }
+            for (int q = 0; q < 32; ++q) stage[(warp * 32 + lane) * ld + cb + q] = any ? __uint_as_float(v[q]) : 0.0f;
+        }
+        __syncthreads();
+        const int* cm = st.cmap >= 0 ? cmaps + st.cmap : nullptr;
+        const int ncols = min(nt, st.N - n0);
+        for (int rr = warp; rr < kTileM; rr += 4) {
+            const int r = m0 + rr;
+            if (r >= st.nrows) break;
+            const uint64_t c = rows[st.row0 + r].c;
+            double* C = S.p[c >> 56] + static_cast<int64_t>(c & 0x00FFFFFFFFFFFFFFull);
+            for (int q = lane; q < ncols; q += 32) {
+                const int n = n0 + q;
+                C[cm ? cm[n] : n] = static_cast<double>(stage[rr * ld + q]);
             }
         }
     } else if (tid == 0) {
@@ -276,7 +286,7 @@ cudaError_t launch_gemm_tc(const Slots& slots, const SlotsF& split, const TcStac
     if (u1 <= u0) return cudaSuccess;
     if (nt != 32 && nt != 64 && nt != 128) return cudaErrorInvalidValue;
     if (wait_polls <= 0) wait_polls = kDefaultWaitPolls;
-    const size_t smem = 2 * kTileBytesA + 2 * kMaxNt * kTileK * 4 + 64;
+    const size_t smem = kSmemBytes;
     static int attr_device = -1;
     int dev = 0;
     cudaGetDevice(&dev);

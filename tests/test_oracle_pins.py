@@ -644,3 +644,39 @@ def test_seniority_closed_forms():
     v = np.zeros(len(basis))
     v[int(np.nonzero(basis == np.uint64(0b11))[0][0])] = 1.0
     assert abs(PR.expectation(PR.seniority_operator(3, 1, 1), v, v)) < 1e-15
+
+
+# ---- approximate M-sector screening (Sec. 2.3.1, closing paragraph) -------------------------
+
+def test_screen_environment_drops_exactly_the_small_label_blocks():
+    """Hand-built environment, one channel, two labels per side: (1,-1) with one index and (1,1)
+    with two.  Sub-block norms 2, 0.05, 1e-3 and 10; tau = 0.01 cuts below 0.1."""
+    q = np.array([[1, -1], [1, 1], [1, 1]])
+    E = np.zeros((3, 1, 3))
+    E[0, 0, 0] = 1e-3                      # ((1,-1), (1,-1))
+    E[0, 0, 1:] = [0.03, 0.04]             # ((1,-1), (1,1)): norm 0.05
+    E[1:, 0, 0] = [1.2, 1.6]               # ((1,1), (1,-1)): norm 2
+    E[1:, 0, 1:] = [[6.0, 0.0], [0.0, 8.0]]  # ((1,1), (1,1)): norm 10
+    out = S.screen_environment(E, q, q, 0.01)
+    expect = E.copy()
+    expect[0, 0, 0] = 0.0
+    expect[0, 0, 1:] = 0.0
+    assert np.array_equal(out, expect)
+    assert np.array_equal(S.screen_environment(E, q, q, 1e-5), E)  # nothing below 1e-4
+
+
+def test_screened_action_reduces_to_the_action_and_error_shrinks_with_tau():
+    K, N, D, G, k = 8, 8, 32, 5, 3
+    labels, tens = inputs.random_mps(K, N, 0, D, 1)
+    P = S.prepare(labels, tens, M.hubbard_mpo(K, 1.0, 4.0), 0, 0, G)
+    P.build_left(k)
+    ql, qr = P.mps.labels[k], P.mps.labels[k + 2]
+    x = np.where(S.two_site_mask(ql, qr), np.random.default_rng(0).standard_normal((ql.shape[0], 4, 4, qr.shape[0])), 0.0)
+    y0, z0 = P.apply(x, k)
+    y, z = P.apply(x, k, screen=1e-14)  # only sub-blocks at the rounding level are dropped
+    assert np.abs(y - y0).max() <= 1e-13 * np.abs(y0).max() and np.abs(z - z0).max() <= 1e-13 * np.abs(z0).max()
+    errs = []
+    for tau in (1e-5, 1e-3, 1e-1):
+        y, z = P.apply(x, k, screen=tau)
+        errs.append(np.abs(y - y0).max() / np.abs(y0).max())
+    assert 0.0 < errs[0] < errs[1] < errs[2]
