@@ -162,72 +162,96 @@ __global__ void __launch_bounds__(128, 3) k_gemm_tc(Slots S, SlotsF F, const TcS
     const int row = m0 + tid;
     const bool rvalid = row < st.nrows;
     const float2 zero = make_float2(0.0f, 0.0f);
-    uint32_t phase = 0;
-    bool failed = false, first = true;
-    for (int s = 0; s < st.nseg && !failed; ++s) {
+    const int nb = nt * kTileK / 128;  // B elements per thread per stage (8, 16 or 32)
+    // K stages run over the segments in order; the operands of stage c + 1 are loaded into
+    // registers while the MMAs of stage c run
+    float2 ra[kTileK], rb[kMaxNt * kTileK / 128];
+    int seg = 0, k0 = 0;       // stage being loaded
+    auto load_stage = [&](int s, int kb) {
         const TcSeg sg = segs[st.seg0 + s];
+        const int kc = min(kTileK, sg.K - kb);
         const uint64_t ah = rvalid ? atab[st.atab0 + static_cast<int64_t>(row) * st.nseg + s] : kNoOperand;
         const float2* __restrict__ A =
             ah == kNoOperand ? nullptr : F.p[ah >> 56] + static_cast<int64_t>(ah & 0x00FFFFFFFFFFFFFFull);
         const float2* __restrict__ B = F.p[sg.b >> 56] + static_cast<int64_t>(sg.b & 0x00FFFFFFFFFFFFFFull);
-        for (int k0 = 0; k0 < sg.K && !failed; k0 += kTileK) {
-            const int kc = min(kTileK, sg.K - k0);
-            // A: one stacked row per thread, 32 K values
-#pragma unroll 8
-            for (int k = 0; k < kTileK; ++k) {
-                const float2 v = (A && k < kc) ? A[k0 + k] : zero;
-                const uint32_t o = kmajor_off(tid, k);
-                *reinterpret_cast<float*>(Ahi + o) = v.x;
-                *reinterpret_cast<float*>(Alo + o) = v.y;
+#pragma unroll
+        for (int k = 0; k < kTileK; ++k) ra[k] = (A && k < kc) ? A[kb + k] : zero;
+        if (sg.b_ks == 1) {  // unit stride along K: lanes along K
+#pragma unroll
+            for (int q = 0; q < kMaxNt * kTileK / 128; ++q) {
+                const int e = q * 128 + tid, n = e / kTileK, k = e % kTileK, col = n0 + n;
+                rb[q] = (q < nb && col < st.N && k < kc)
+                            ? B[static_cast<int64_t>(kb + k) + static_cast<int64_t>(col) * sg.b_ns]
+                            : zero;
             }
-            // B: nt rows (columns of C) x 32 K values, the unit-stride index fastest
-            if (sg.b_ks == 1) {
-                for (int e = tid; e < nt * kTileK; e += blockDim.x) {
-                    const int n = e / kTileK, k = e % kTileK, col = n0 + n;
-                    const float2 v = (col < st.N && k < kc)
-                                         ? B[static_cast<int64_t>(k0 + k) + static_cast<int64_t>(col) * sg.b_ns]
-                                         : zero;
-                    const uint32_t o = kmajor_off(n, k);
-                    *reinterpret_cast<float*>(Bhi + o) = v.x;
-                    *reinterpret_cast<float*>(Blo + o) = v.y;
-                }
-            } else {
-                for (int e = tid; e < nt * kTileK; e += blockDim.x) {
-                    const int n = e % nt, k = e / nt, col = n0 + n;
-                    const float2 v = (col < st.N && k < kc)
-                                         ? B[static_cast<int64_t>(k0 + k) * sg.b_ks + static_cast<int64_t>(col) * sg.b_ns]
-                                         : zero;
-                    const uint32_t o = kmajor_off(n, k);
-                    *reinterpret_cast<float*>(Bhi + o) = v.x;
-                    *reinterpret_cast<float*>(Blo + o) = v.y;
-                }
+        } else {  // lanes along N
+#pragma unroll
+            for (int q = 0; q < kMaxNt * kTileK / 128; ++q) {
+                const int e = q * 128 + tid, n = e % nt, k = e / nt, col = n0 + n;
+                rb[q] = (q < nb && col < st.N && k < kc)
+                            ? B[static_cast<int64_t>(kb + k) * sg.b_ks + static_cast<int64_t>(col) * sg.b_ns]
+                            : zero;
             }
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t ah0 = saddr(Ahi), al0 = saddr(Alo), bh0 = saddr(Bhi), bl0 = saddr(Blo);
-                const int nk = (kc + 7) / 8;
-                for (int kk = 0; kk < nk; ++kk) {
-                    const uint32_t ko = static_cast<uint32_t>(kk) * 256;
-                    mma_tf32(tmem, kdesc(ah0 + ko), kdesc(bh0 + ko), idesc, first ? 0u : 1u);
-                    first = false;
-                    if (SPLIT3) {
-                        mma_tf32(tmem, kdesc(ah0 + ko), kdesc(bl0 + ko), idesc, 1u);
-                        mma_tf32(tmem, kdesc(al0 + ko), kdesc(bh0 + ko), idesc, 1u);
-                    }
-                }
-                *issued = 1;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    saddr(mbar)));
-                // the stage buffers are reused by the next K stage: wait for these MMAs
-                *flag = poll(saddr(mbar), phase, wait_polls);
-                if (!*flag) atomicExch(err, 1);
-            }
-            __syncthreads();
-            if (!*flag) failed = true;
-            phase ^= 1u;
         }
+    };
+    auto store_stage = [&](int b_ks) {
+#pragma unroll
+        for (int k = 0; k < kTileK; ++k) {
+            const uint32_t o = kmajor_off(tid, k);
+            *reinterpret_cast<float*>(Ahi + o) = ra[k].x;
+            *reinterpret_cast<float*>(Alo + o) = ra[k].y;
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxNt * kTileK / 128; ++q) {
+            if (q >= nb) break;
+            const int e = q * 128 + tid;
+            const int n = b_ks == 1 ? e / kTileK : e % nt, k = b_ks == 1 ? e % kTileK : e / nt;
+            const uint32_t o = kmajor_off(n, k);
+            *reinterpret_cast<float*>(Bhi + o) = rb[q].x;
+            *reinterpret_cast<float*>(Blo + o) = rb[q].y;
+        }
+    };
+    uint32_t phase = 0;
+    bool failed = false, first = true;
+    if (st.nseg > 0) load_stage(0, 0);
+    while (seg < st.nseg && !failed) {
+        const TcSeg sg = segs[st.seg0 + seg];
+        const int kc = min(kTileK, sg.K - k0);
+        store_stage(sg.b_ks);
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ah0 = saddr(Ahi), al0 = saddr(Alo), bh0 = saddr(Bhi), bl0 = saddr(Blo);
+            const int nk = (kc + 7) / 8;
+            for (int kk = 0; kk < nk; ++kk) {
+                const uint32_t ko = static_cast<uint32_t>(kk) * 256;
+                mma_tf32(tmem, kdesc(ah0 + ko), kdesc(bh0 + ko), idesc, first ? 0u : 1u);
+                first = false;
+                if (SPLIT3) {
+                    mma_tf32(tmem, kdesc(ah0 + ko), kdesc(bl0 + ko), idesc, 1u);
+                    mma_tf32(tmem, kdesc(al0 + ko), kdesc(bh0 + ko), idesc, 1u);
+                }
+            }
+            *issued = 1;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                saddr(mbar)));
+        }
+        // next stage: advance and load its operands while the MMAs run
+        k0 += kTileK;
+        if (k0 >= sg.K) {
+            ++seg;
+            k0 = 0;
+        }
+        if (seg < st.nseg) load_stage(seg, k0);
+        if (tid == 0) {
+            // the stage buffers are reused by the next K stage: wait for these MMAs
+            *flag = poll(saddr(mbar), phase, wait_polls);
+            if (!*flag) atomicExch(err, 1);
+        }
+        __syncthreads();
+        if (!*flag) failed = true;
+        phase ^= 1u;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!failed) {

@@ -2,7 +2,8 @@
 
 ``hubbard_chain_handles`` prepares the L=24, D=256, n_beta=8 Hubbard workload (targets S=0 and
 S=1) the way the benchmark does: seeded random MPS, GPU canonicalisation, warm-up sweeps,
-checkpoint.  ``python -m paper_1703_04789_gb300.workloads --sweeps W --applies A`` runs the
+checkpoint.  ``ab_initio_action`` runs one projected action of the K=20, N=30, 2M=2S=10,
+n_beta=12 active-space workload at a given bond dimension (``--ab-initio-D 100 200``).  ``python -m paper_1703_04789_gb300.workloads --sweeps W --applies A`` runs the
 warm-up sweeps and then A projected actions at the middle site of the optimised MPS, so that a
 profiler can capture the block-GEMM launches of a converged state; with ``--profile-sweep`` it
 also runs one more full sweep of the S=0 target inside the NVTX range ``profile_sweep`` (the
@@ -32,8 +33,53 @@ def hubbard_chain_handles(warm_sweeps: int, spec=HUBBARD_L24, targets=None, **op
     return out
 
 
+AB_INITIO_K20 = {"K": 20, "N": 30, "twoM": 10, "twoS": 10, "n_beta": 12, "seed": 3}
+
+
+def ab_initio_action(D: int, spec=AB_INITIO_K20, precisions=("fp64", "3xtf32"), site=None, m_screen=0.0):
+    """One projected action at the middle of the synthetic active-space workload (K=20, N=30,
+    2M=2S=10, n_beta=12; integrals from inputs.synthetic_active_space) for a seeded random MPS of
+    bond dimension D, canonicalised on the GPU: per precision form the phase times (CUDA events),
+    the algorithmic flops and bytes, the error of y against the FP64 action, and the device memory
+    in use (environments of every bond, the action's intermediates)."""
+    import torch
+    from . import Spmps, inputs
+    K, N, twoM, twoS, G = spec["K"], spec["N"], spec["twoM"], spec["twoS"], spec["n_beta"]
+    h1, eri, ecore = inputs.synthetic_active_space(K, spec["seed"])
+    labels, tens = inputs.random_mps(K, N, twoM, D, spec["seed"])
+    k = K // 2 - 1 if site is None else site
+    out = {"K": K, "N": N, "twoM": twoM, "twoS": twoS, "n_beta": G, "D": D, "site": k, "m_screen": m_screen,
+           "forms": {}}
+    y64 = None
+    for prec in precisions:
+        dev = Spmps(K, N, twoM, twoS, G, D, precision=prec, autotune=False, m_screen=m_screen)
+        dev.set_hamiltonian(h1, eri, ecore)
+        dev.set_mps(labels, tens, center=0)
+        dev.canonicalize()
+        lay = dev.x_layout(k)
+        x = torch.tensor(np.random.default_rng(1).standard_normal(lay["n_x"]), device="cuda")
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        dev.apply_heff(k, x, y, z)
+        torch.cuda.synchronize()
+        free, total = torch.cuda.mem_get_info()
+        ms = np.mean([dev.apply_heff_timed(k, x, y, z) for _ in range(2)], axis=0)
+        fl, by = dev.apply_costs(k)
+        yv = y.cpu().numpy()
+        if prec == "fp64":
+            y64 = yv
+        out["forms"][prec] = {"n_x": lay["n_x"], "phase_ms": [round(float(v), 4) for v in ms],
+                              "flops": fl.tolist(), "bytes": by.tolist(),
+                              "device_memory_used_GB": round((total - free) / 1e9, 2),
+                              "rel_err_y_vs_fp64": None if y64 is None else float(np.abs(yv - y64).max() / np.abs(y64).max())}
+        dev.close()
+        torch.cuda.synchronize()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--ab-initio-D", type=int, nargs="*", default=None,
+                    help="one action of the K=20 active-space workload at each of these bond dimensions")
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--applies", type=int, default=3)
     ap.add_argument("--site", type=int, default=11)
@@ -44,6 +90,11 @@ def main():
     import torch
     from . import build
     build.build()
+    if args.ab_initio_D:
+        import json
+        for D in args.ab_initio_D:
+            print(json.dumps(ab_initio_action(D)), flush=True)
+        return
     h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune, precision=args.precision)[0]
     dev = h["dev"]
     lay = dev.x_layout(args.site)
