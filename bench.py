@@ -53,7 +53,9 @@ WORKLOAD = {
     "mps": "seeded random (N,M)-symmetric MPS, inputs.random_mps(seed=2), canonicalised on the GPU",
     "davidson": "|r| < 1e-6 and |dtheta| < 1e-10, subspace 20, cap 200",
     "forms": {"fast": "grouped launches over all beta points and blocks, autotuned GEMM tiles, H part of the "
-                      "block products in 3xTF32 on the tensor cores until |r| < 1e-5, then FP64; diagonal correction",
+                      "block products in 3xTF32 on the tensor cores (stacked tcgen05 GEMM) until |r| < 1e-5, then "
+                      "FP64; diagonal correction",
+              "fast_mma_sync": "fast with the warp-level mma.sync tensor-core kernel",
               "fp64_plain": "one launch per beta point and phase, fixed tiles, FP64, diagonal correction",
               "fast_fp64": "fast with every block product in FP64",
               "fast_learned": "fast with the learned Davidson correction"},
@@ -181,6 +183,8 @@ FORMS = {
     "fp64_plain": dict(batched=False, autotune=False, precision="fp64", precond="diag"),
     "fast_fp64": dict(batched=True, autotune=True, precision="fp64", precond="diag"),
     "fast_learned": dict(batched=True, autotune=True, precision="3xtf32", precond="learned"),
+    "fast_mma_sync": dict(batched=True, autotune=True, precision="3xtf32", precond="diag",
+                          tensor_core_kernel="mma_sync"),
 }
 
 
@@ -279,7 +283,7 @@ def run_ours(args):
         res_plain.append(_time_sweeps(d, h["ckpt"], 1, flush, torch))
         d.close()
     variants = {}
-    for form in ("fast_fp64", "fast_learned"):
+    for form in ("fast_fp64", "fast_mma_sync", "fast_learned"):
         d = _handle(form, hs[0]["twoM"], hs[0]["twoS"], params)
         r = _time_sweeps(d, hs[0]["ckpt"], 1, flush, torch)
         d.close()
@@ -288,7 +292,7 @@ def run_ours(args):
                           "abs_dE_vs_fp64_plain": abs(r["E"][0] - res_plain[0]["E"][0])}
 
     peak = device_fp64_peak(torch.cuda.current_device())
-    tf32_sync = device_tf32_peak(0)
+    tf32_peaks = (device_tf32_peak(0), device_tf32_peak(1))
     hbm = _measured_peaks().get("hbm_gbs")
     if rank != 0:
         return
@@ -313,7 +317,7 @@ def run_ours(args):
         "variants_2S=0": variants,
         "learned_correction": mlp_info,
         "apply_tflops": round(apply_flops / (total_ms * 1e-3) / 1e12, 6),
-        "roofline": _roofline(phase_tc, phase, fl_op, by_op, hbm, tf32_sync, peak, breakdown),
+        "roofline": _roofline(phase_tc, phase, fl_op, by_op, hbm, tf32_peaks, peak, breakdown),
         "time_breakdown_ms": dict(breakdown, timed_sweeps_total_ms=round(total_ms, 2)),
         "e2e": {"value": round(e2e_value, 6), "unit": "sweeps/s", "h2d_bytes_per_step": sum(h["ckpt_bytes"] for h in hs),
                 "d2h_bytes_per_step": 8 * len(hs)},
@@ -335,40 +339,48 @@ def _measured_peaks():
         return {}
 
 
-def _roofline(phase_tc, phase64, fl_op, by_op, hbm, tf32_sync, fp64_peak, breakdown):
-    """Roofline of the fast form's dominant kernel, k_gemm_tf32s (the 3xTF32 H products of phases
-    A and C), timed alone at the middle site (H part only, so the events bracket its launches):
-    achieved = algorithmic bytes of those phases / their event time against the measured HBM copy
-    bandwidth (the reductions are 5-60 long, so the products are far below the tensor pipe's
-    ridge point; the flop rate against the measured mma.sync TF32 peak is given beside it), and
-    k_gemm_f64 (the FP64 action, phases A and C of H and N) against the measured FP64 peak."""
+def _roofline(phase_tc, phase64, fl_op, by_op, hbm, tf32_peaks, fp64_peak, breakdown):
+    """Roofline of the fast form's dominant kernel and of its tensor-core kernel.
+
+    The kernel breakdown of a fast sweep (separate profiled pass) puts the FP64 block GEMMs first:
+    the N_eff products, the FP64 finish of every Davidson solve, the environment updates and the
+    decimation density matrices all run in k_gemm_f64, which is bound by the FP64 pipe
+    ("alu": achieved = algorithmic flops of phases A and C of the middle-site FP64 action / their
+    CUDA-event time, against the FP64 FMA peak measured on all SMs).  The tensor-core products of
+    the H part (stacked tcgen05 GEMM, k_gemm_tc) are reported beside it against the measured HBM
+    copy bandwidth (their reductions are 5 to a few hundred long: far below the tensor pipe's
+    ridge point) and against the measured tcgen05 kind::tf32 peak."""
+    t64 = (phase64[1] + phase64[3]) * 1e-3
+    flops64 = float(fl_op[0][0] + fl_op[0][2] + fl_op[1][0] + fl_op[1][2])
     t_tc = (phase_tc[1] + phase_tc[3]) * 1e-3
     bytes_tc = float(by_op[0][0] + by_op[0][2])
     flops_tc = float(fl_op[0][0] + fl_op[0][2])
-    t64 = (phase64[1] + phase64[3]) * 1e-3
-    flops64 = float(fl_op[0][0] + fl_op[0][2] + fl_op[1][0] + fl_op[1][2])
     peak_bw = hbm if hbm else 6800.0
-    achieved = bytes_tc / t_tc / 1e9
-    gt = breakdown.get("gemm_tensor_core", {})
     g64 = breakdown.get("gemm_fp64", {})
+    gtc = breakdown.get("gemm_tensor_core", {})
+    total = breakdown.get("profiled_sweep_ms") or 0.0
+    ach64 = flops64 / t64 / 1e12
     return {
-        "bound": "hbm", "kernel": "k_gemm_tf32s: 3xTF32 H products of phases A and C at sites (11, 12), S=0",
-        "achieved": round(achieved, 2), "peak": round(peak_bw, 1), "unit": "GB/s",
-        "frac": round(achieved / peak_bw, 4),
-        "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800 GB/s",
-        "traffic": None,
-        "algorithmic_bytes_per_action": bytes_tc, "phase_ms": [round(float(v), 4) for v in phase_tc],
-        "tensor": {"achieved_tflops": round(flops_tc / t_tc / 1e12, 4),
-                   "peak_tflops_mma_sync_tf32": round(tf32_sync, 2),
-                   "frac": round(flops_tc / t_tc / 1e12 / tf32_sync, 5) if tf32_sync else None,
-                   "note": "algorithmic flops (one product per multiply-add, 3xTF32 split not counted)"},
-        "fp64_kernel": {"kernel": "k_gemm_f64, phases A and C of the FP64 action (H and N)", "bound": "alu",
-                        "achieved": round(flops64 / t64 / 1e12, 6), "peak": round(fp64_peak, 6), "unit": "TFLOP/s",
-                        "frac": round(flops64 / t64 / 1e12 / fp64_peak, 4) if fp64_peak else None,
-                        "peak_source": "measured FP64 FMA-chain kernel on all SMs (spmps_device_fp64_peak)",
-                        "phase_ms": [round(float(v), 4) for v in phase64]},
-        "sweep_share": {"gemm_tensor_core_ms": gt.get("ms"), "gemm_fp64_ms": g64.get("ms"),
-                        "profiled_sweep_ms": breakdown.get("profiled_sweep_ms")},
+        "bound": "alu", "kernel": "k_gemm_f64: phases A and C of the FP64 projected action (H and N) at sites (11, 12), S=0",
+        "achieved": round(ach64, 6), "peak": round(fp64_peak, 6), "unit": "TFLOP/s",
+        "frac": round(ach64 / fp64_peak, 4) if fp64_peak else None,
+        "peak_source": "measured: FP64 FMA-chain kernel on all SMs (spmps_device_fp64_peak; nominal 1.25)",
+        "traffic": TRAFFIC_PER_LAUNCH,
+        "traffic_note": "dram bytes read + written per k_gemm_f64 launch (mean of the phase-A and phase-C launches) "
+                        "from one ncu capture of the middle-site action",
+        "phase_ms": [round(float(v), 4) for v in phase64],
+        "share_of_fast_sweep": round(g64.get("ms", 0.0) / total, 4) if total else None,
+        "tensor_core_kernel": {
+            "kernel": "k_gemm_tc: stacked tcgen05 kind::tf32 (3xTF32) H products of phases A and C, same site",
+            "bound": "hbm", "achieved_GBs": round(bytes_tc / t_tc / 1e9, 2), "peak_GBs": round(peak_bw, 1),
+            "frac": round(bytes_tc / t_tc / 1e9 / peak_bw, 4),
+            "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800 GB/s",
+            "algorithmic_bytes": bytes_tc, "phase_ms": [round(float(v), 4) for v in phase_tc],
+            "achieved_tflops": round(flops_tc / t_tc / 1e12, 4),
+            "peak_tflops_tcgen05_tf32": round(tf32_peaks[1], 1), "peak_tflops_mma_sync_tf32": round(tf32_peaks[0], 1),
+            "tensor_frac": round(flops_tc / t_tc / 1e12 / tf32_peaks[1], 5) if tf32_peaks[1] else None,
+            "share_of_fast_sweep": round(gtc.get("ms", 0.0) / total, 4) if total else None,
+            "note": "algorithmic flops (one product per multiply-add; the 3xTF32 split is not counted)"},
     }
 
 
