@@ -231,8 +231,10 @@ spmps_status spmps_device_fp64_peak(int device, double* tflops);
  * `sms` SMs (0 = all), one CTA per SM: kind 0 = the warp-level mma.sync.m16n8k8 TF32 instruction
  * with FP32 accumulation (32 warps, 8 independent chains per warp), kind 1 =
  * tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, operands in shared memory, accumulator in tensor
- * memory, issued by one thread of one CTA per SM.  The roofline denominators of the reduced-precision
- * action.  SPMPS_ERR_TIMEOUT if the bounded wait for the tcgen05 MMAs gave up. */
+ * memory, issued by one thread of one CTA per SM; kind 2 = the warp-level INT8 instruction
+ * mma.sync.m16n8k32 s8 x s8 -> s32 (tera-operations per second: the rate an integer-split FP64
+ * emulation would build on).  The roofline denominators of the reduced-precision action.
+ * SPMPS_ERR_TIMEOUT if the bounded wait for the tcgen05 MMAs gave up. */
 spmps_status spmps_device_tf32_peak(int device, int kind, int sms, double* tflops);
 
 /* The same projected action as spmps_apply_heff, for callers that cannot let the library allocate
@@ -378,6 +380,20 @@ spmps_status spmps_mlp_train(spmps_handle h, int steps, int batch, double lr, ui
  * runs the BF16 tensor-core path used inside Davidson, 0 an FP32 reference path. */
 spmps_status spmps_mlp_infer(spmps_handle h, const double* r, const double* dh, const double* dn, double theta,
                              int64_t n, double* t, int tensor_cores);
+
+/* ---- State-specific excited states (Sec. 2.3.2, Eq. orthoB, Fig. spmpsex) ---------------------
+ * spmps_add_lower_state: a lower state |Psi_j> (an MPS with the handle's K, N and 2M, format of
+ *   spmps_set_mps; copied; at most 16).  From then on every two-site step (spmps_sweep,
+ *   spmps_optimize_step) builds B_j = <Psi_j| P |d Psi / d x> at its sites from per-beta
+ *   environments between the running state (bra) and |Psi_j> (ket), orthonormalises the B_j (QR by
+ *   Gram-Schmidt twice) into V and solves Eq. geproblem in the range of Q = 1 - V V^T: the start
+ *   vector, the residual and every new Davidson direction are projected with Q, so the optimised
+ *   state keeps <Psi_j|P|Psi> = 0.  Adding a lower state invalidates the handle's environments.
+ * spmps_clear_lower_states: back to the ground-state problem.
+ * spmps_lower_overlap: <Psi_j| P |Psi> of the current MPS (B_j . x at the centre pair). */
+spmps_status spmps_add_lower_state(spmps_handle h, const int* bond_dims, const int* labels, const double* const* sites);
+spmps_status spmps_clear_lower_states(spmps_handle h);
+spmps_status spmps_lower_overlap(spmps_handle h, int j, double* value);
 
 /* Quadrature used by the handle: beta_g and c_g (n_beta each, host arrays). */
 spmps_status spmps_quadrature(spmps_handle h, double* beta, double* c);

@@ -303,7 +303,7 @@ class DavidsonResult:
 def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
              max_sub=20, max_iter=200, eps_metric=1e-12, clamp=1e-4,
              precond="diag", apply_n=None, cg_steps=5, metric_blocks=None,
-             metric_shift=METRIC_SHIFT) -> DavidsonResult:
+             metric_shift=METRIC_SHIFT, constraints=None) -> DavidsonResult:
     """Lowest eigenpair of H x = theta N x with N positive semi-definite.
 
     Basis V Euclidean-orthonormal (classical Gram-Schmidt applied twice); Ritz problem
@@ -317,7 +317,9 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
     inverse of N shifted by metric_shift, which keeps directions of N-norm down to ~metric_shift;
     entries of blocks left out keep the diagonal correction);
     restart from [x, previous x] when the basis reaches max_sub; converged when
-    ||r|| < tol_r and |theta - theta_prev| < tol_theta."""
+    ||r|| < tol_r and |theta - theta_prev| < tol_theta.  ``constraints`` (orthonormal columns V over
+    the masked entries, or None): the start vector and every correction are projected with
+    Q = 1 - V V^T, so the solve stays in the range of Q (excited states, Eq. orthoB)."""
     shape = x0.shape
     sel = mask.reshape(-1)
     v = x0.reshape(-1)[sel]
@@ -334,6 +336,8 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
         full[sel] = u
         return apply_n(full.reshape(shape)).reshape(-1)[sel]
 
+    Qc = (lambda u: u - constraints @ (constraints.T @ u)) if constraints is not None else (lambda u: u)
+    v = Qc(Qc(v))
     V = (v / np.linalg.norm(v))[:, None]
     y, z = op(V[:, 0])
     HV, NV = y[:, None], z[:, None]
@@ -357,7 +361,7 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
         c = X @ C[:, 0]
         x = V @ c
         hx, nx = HV @ c, NV @ c
-        r = hx - theta * nx
+        r = Qc(hx - theta * nx)  # with constraints: the residual within the range of Q
         rn = np.linalg.norm(r)
         if rn < tol_r and abs(theta - theta_prev) < tol_theta:
             full = np.zeros(sel.shape[0])
@@ -383,11 +387,13 @@ def davidson(apply_hn, x0, diag_h, diag_n, mask, tol_r=1e-6, tol_theta=1e-10,
             Cb = V.T @ B
             Qb, _ = np.linalg.qr(Cb)
             V, HV, NV = V @ Qb, HV @ Qb, NV @ Qb
+        t = Qc(t)
         for _ in range(2):
             t = t - V @ (V.T @ t)
+        t = Qc(t)
         tn = np.linalg.norm(t)
         if tn < 1e-14:
-            t = r.copy()
+            t = Qc(r.copy())
             for _ in range(2):
                 t = t - V @ (V.T @ t)
             tn = np.linalg.norm(t)

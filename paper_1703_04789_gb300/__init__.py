@@ -88,6 +88,9 @@ def load_library(path: str | None = None):
         "spmps_device_fp64_peak": (i, [i, P(d)]),
         "spmps_device_tf32_peak": (i, [i, i, i, P(d)]),
         "spmps_apply_costs": (i, [H, i, P(d), P(d)]),
+        "spmps_add_lower_state": (i, [H, P(i), P(i), C.c_void_p]),
+        "spmps_clear_lower_states": (i, [H]),
+        "spmps_lower_overlap": (i, [H, i, P(d)]),
         "spmps_two_site": (i, [H, i, C.c_void_p]),
         "spmps_canonicalize": (i, [H]),
         "spmps_sweep": (i, [H, i, P(d)]),
@@ -207,6 +210,25 @@ class Spmps:
         self._check(self.lib.spmps_set_mps(self._h, dims.ctypes.data_as(C.POINTER(C.c_int)),
                                            lab.ctypes.data_as(C.POINTER(C.c_int)), arr, center))
         self._keep = ts
+
+    # ---- excited states ------------------------------------------------------------------------
+    def add_lower_state(self, labels, tensors):
+        """A lower state to stay orthogonal to (in the projected metric, Eq. orthoB); format of set_mps."""
+        dims = np.array([l.shape[0] for l in labels], dtype=np.int32)
+        lab = np.ascontiguousarray(np.concatenate([np.asarray(l, dtype=np.int32).reshape(-1, 2) for l in labels]))
+        ts = [np.ascontiguousarray(t, dtype=np.float64) for t in tensors]
+        arr = (C.POINTER(C.c_double) * len(ts))(*[_dptr(t) for t in ts])
+        self._check(self.lib.spmps_add_lower_state(self._h, dims.ctypes.data_as(C.POINTER(C.c_int)),
+                                                   lab.ctypes.data_as(C.POINTER(C.c_int)), arr))
+
+    def clear_lower_states(self):
+        self._check(self.lib.spmps_clear_lower_states(self._h))
+
+    def lower_overlap(self, j: int = 0) -> float:
+        """<Psi_j| P |Psi> of the current MPS."""
+        v = C.c_double()
+        self._check(self.lib.spmps_lower_overlap(self._h, j, C.byref(v)))
+        return v.value
 
     # ---- layout -------------------------------------------------------------------------------
     def x_layout(self, site: int):
@@ -502,8 +524,8 @@ def mpo_from_integrals(h1, h2=None, ecore: float = 0.0):
 
 
 def device_tf32_peak(kind: int, sms: int = 0, device: int = 0) -> float:
-    """Measured dense TF32 tensor-core throughput (TFLOP/s): kind 0 = mma.sync.m16n8k8, kind 1 =
-    tcgen05.mma kind::tf32; on `sms` SMs (0 = all)."""
+    """Measured dense tensor-core throughput (TFLOP/s): kind 0 = TF32 mma.sync.m16n8k8, kind 1 =
+    tcgen05.mma kind::tf32, kind 2 = INT8 mma.sync.m16n8k32 (TOP/s); on `sms` SMs (0 = all)."""
     lib = load_library()
     v = C.c_double()
     st = lib.spmps_device_tf32_peak(device, kind, sms, C.byref(v))

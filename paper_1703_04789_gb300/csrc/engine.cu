@@ -1195,6 +1195,7 @@ void invalidate_all(spmps_t* h) {
     for (auto& e : h->Lenv) e.valid = false;
     for (auto& e : h->Renv) e.valid = false;
     for (auto& p : h->apply_plans) p.reset();
+    excited_invalidate(h);
 }
 
 // Autotuner: time every tile candidate for phases A and C of the site's action plan (one warm-up

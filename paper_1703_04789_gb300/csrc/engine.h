@@ -127,6 +127,18 @@ struct Plan {
 
 }  // namespace spmps
 
+// A lower state of a state-specific excited-state optimisation (Sec. 2.3.2): its MPS (fixed) and
+// the per-beta environments of <running state| exp(+i b_g S_y) |lower state> (bra = the state
+// being optimised, ket = the lower state, the identity MPO rotated by -beta_g, one channel), from
+// which the B vector of Eq. orthoB follows at every two-site step.
+struct LowerState {
+    std::vector<spmps::Bond> bonds;
+    std::vector<spmps::RowBlockLayout> alay;
+    std::vector<std::unique_ptr<spmps::DevMem>> A;
+    std::vector<spmps::MPO> rot;  // per beta point
+    std::vector<spmps::EnvStore> L, R;
+};
+
 // State of the learned Davidson correction.
 struct MlpState {
     spmps::DevMem params, grads, m, v, w2core, err;
@@ -154,6 +166,7 @@ struct spmps_t {
     // orders a caller's stream after the handle's stream in spmps_apply_heff_noalloc
     cudaEvent_t noalloc_order = nullptr;
     spmps::DevMem tc_err;  // set by the stacked tensor-core GEMM when a bounded wait gave up
+    std::vector<LowerState> lower;  // lower states of an excited-state optimisation (Eq. orthoB)
     std::vector<double> beta, cg;
 
     bool has_ham = false, has_mps = false;
@@ -211,6 +224,13 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
                       const SlotsF* split = nullptr);
 spmps_status update_left(spmps_t* h, int i);
 spmps_status env_subblock_norms(spmps_t* h, const EnvStore& E, const Bond& b, int bond, EnvNorms& out);
+// Excited states: the B vectors of every lower state at sites (k, k+1), orthonormalised (QR by
+// Gram-Schmidt twice) into V (n_x x count, device); *count = number of independent columns.
+spmps_status excited_constraints(spmps_t* h, int k, DevMem& V, int* count);
+// The cross environments follow the running MPS: after a decimation at k (move_right: left
+// environment of bond k+1; else right environment of bond k+1).
+spmps_status excited_after_step(spmps_t* h, int k, bool move_right);
+void excited_invalidate(spmps_t* h);
 spmps_status update_right(spmps_t* h, int i);
 spmps_status ensure_envs(spmps_t* h, int k);
 void invalidate_all(spmps_t* h);

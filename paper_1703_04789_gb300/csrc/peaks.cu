@@ -37,6 +37,30 @@ __global__ void __launch_bounds__(1024) k_mma_sync_tf32_peak(int iters, float* o
     if (s == 1234.5f) out[0] = s;  // keeps the chains alive
 }
 
+// INT8 (s8 x s8 -> s32) warp-level MMAs, 8 independent chains per warp: the integer rate that an
+// Ozaki-style FP64 emulation (exact integer products of split mantissas) would run at.
+__global__ void __launch_bounds__(1024) k_mma_sync_s8_peak(int iters, int* out) {
+    uint32_t a[4], b[2];
+    for (int q = 0; q < 4; ++q) a[q] = 0x01020304u * (threadIdx.x + q + 1);
+    for (int q = 0; q < 2; ++q) b[q] = 0x01010101u * (threadIdx.x + q + 1);
+    int acc[8][4];
+    for (int c = 0; c < 8; ++c)
+        for (int q = 0; q < 4; ++q) acc[c][q] = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+r"(acc[c][0]), "+r"(acc[c][1]), "+r"(acc[c][2]), "+r"(acc[c][3])
+                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+    int s = 0;
+    for (int c = 0; c < 8; ++c)
+        for (int q = 0; q < 4; ++q) s += acc[c][q];
+    if (s == 12345) out[0] = s;
+}
+
 constexpr int kPeakM = 128, kPeakN = 256, kPeakK = 32;  // smem tiles: A 128 x 32, B 256 x 32 (tf32)
 constexpr int kPeakSmem = (kPeakM + kPeakN) * kPeakK * 4 + 64;
 
@@ -122,7 +146,7 @@ __global__ void __launch_bounds__(128, 1) k_tcgen05_tf32_peak(int iters, float* 
 }  // namespace
 
 extern "C" spmps_status spmps_device_tf32_peak(int device, int kind, int sms, double* tflops) {
-    if (!tflops || kind < 0 || kind > 1 || sms < 0) return SPMPS_ERR_BAD_INPUT;
+    if (!tflops || kind < 0 || kind > 2 || sms < 0) return SPMPS_ERR_BAD_INPUT;
     if (cudaSetDevice(device) != cudaSuccess) return SPMPS_ERR_CUDA;
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return SPMPS_ERR_CUDA;
@@ -148,6 +172,13 @@ extern "C" spmps_status spmps_device_tf32_peak(int device, int kind, int sms, do
         k_mma_sync_tf32_peak<<<blocks, threads>>>(iters, out);
         cudaEventRecord(e1);
         flops = 2.0 * 16 * 8 * 8 * 8.0 * iters * (threads / 32) * static_cast<double>(blocks);
+    } else if (kind == 2) {
+        const int threads = 1024, iters = 1 << 13;
+        k_mma_sync_s8_peak<<<blocks, threads>>>(64, reinterpret_cast<int*>(out));
+        cudaEventRecord(e0);
+        k_mma_sync_s8_peak<<<blocks, threads>>>(iters, reinterpret_cast<int*>(out));
+        cudaEventRecord(e1);
+        flops = 2.0 * 16 * 8 * 32 * 8.0 * iters * (threads / 32) * static_cast<double>(blocks);
     } else {
         const int iters = 1 << 12;
         e = cudaFuncSetAttribute(k_tcgen05_tf32_peak, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem);

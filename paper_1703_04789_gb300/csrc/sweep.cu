@@ -48,7 +48,20 @@ int64_t x_size(spmps_t* h, int k) { return make_row_block_layout(h->bonds[k], h-
 struct DavBuffers {
     DevMem V, HV, NV, hm, nm, coef, coef_prev, scal, x, hx, nx, r, t, dh, dn, Q, tmp, cg_p, cg_ap, cg_res, dot, ritz;
     MetricState metric;  // factors of the metric blocks (precond == 4)
+    DevMem Vc;           // orthonormal constraint vectors (excited states, Eq. orthoB)
+    int ncon = 0;
 };
+
+// t <- (1 - Vc Vc^T) t, twice (excited states: the solve stays in the range of Q)
+spmps_status project_constraints(spmps_t* h, DavBuffers& B, int64_t n, double* t) {
+    for (int pass = 0; pass < 2 && B.ncon > 0; ++pass) {
+        CK(launch_multidot(B.Vc.as<double>(), n, B.ncon, t, n, B.dot.as<double>() + 32, h->partial.as<double>(),
+                           h->stream));
+        CK(launch_gemv(B.Vc.as<double>(), n, B.ncon, B.dot.as<double>() + 32, n, t, 1, h->stream));
+        h->launches += 3;
+    }
+    return SPMPS_OK;
+}
 
 spmps_status ensure_dav(spmps_t* h, DavBuffers& B, int64_t n, int ms) {
     const size_t v = static_cast<size_t>(std::max<int64_t>(n, 1)) * sizeof(double);
@@ -128,6 +141,12 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
 
 spmps_status davidson(spmps_t* h, int k, const double* x0, DavBuffers& B, DavidsonOut* out) {
     B.metric.ok = false;
+    B.ncon = 0;
+    if (!h->lower.empty()) {
+        // excited state: the B vectors of the lower states at this step, orthonormalised (Eq. orthoB)
+        spmps_status st = excited_constraints(h, k, B.Vc, &B.ncon);
+        if (st != SPMPS_OK) return st;
+    }
     if (h->opt.precond == 4) {
         // factors of the metric blocks for the correction (environments built first)
         Plan* P = nullptr;
@@ -179,6 +198,8 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
     double* V = B.V.as<double>();
     double* sc = B.scal.as<double>();
     CK(cudaMemcpyAsync(V, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    st = project_constraints(h, B, n, V);
+    if (st != SPMPS_OK) return st;
     CK(launch_norm2(V, n, sc + 3, h->partial.as<double>(), h->stream));
     CK(launch_scale_inv_sqrt(V, n, sc + 3, h->stream));
     h->launches += 3;
@@ -265,6 +286,15 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         CK(launch_residual_diag(B.hx.as<double>(), B.nx.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, kClamp,
                                 n, B.r.as<double>(), B.t.as<double>(), sc + 2, h->partial.as<double>(), h->stream));
         h->launches += 7;
+        if (B.ncon > 0) {
+            // the residual within the range of Q, its norm and the diagonal correction of it
+            st = project_constraints(h, B, n, B.r.as<double>());
+            if (st != SPMPS_OK) return st;
+            CK(launch_norm2(B.r.as<double>(), n, sc + 2, h->partial.as<double>(), h->stream));
+            CK(launch_precond_apply(B.r.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, kClamp, n,
+                                    B.t.as<double>(), h->stream));
+            h->launches += 3;
+        }
         if (rec >= 0) prof_end(h, h->stream, rec);
         if (h->opt.precond == 1) {
             st = metric_cg(h, k, B, n, B.r.as<double>(), B.t.as<double>());
@@ -337,6 +367,8 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         // new direction into column m: t orthogonalised twice against V, normalised
         double* tcol = V + static_cast<int64_t>(m) * n;
         CK(cudaMemcpyAsync(tcol, tsrc, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        st = project_constraints(h, B, n, tcol);
+        if (st != SPMPS_OK) return st;
         for (int pass = 0; pass < 2; ++pass) {
             CK(launch_multidot(V, n, m, tcol, n, B.dot.as<double>(), h->partial.as<double>(), h->stream));
             CK(launch_gemv(V, n, m, B.dot.as<double>(), n, tcol, 1, h->stream));
@@ -847,6 +879,8 @@ spmps_status spmps_optimize_step(spmps_handle h, int site, int move_right, doubl
         h->center = site;
     }
     if (st != SPMPS_OK) return st;
+    st = excited_after_step(h, site, move_right != 0);
+    if (st != SPMPS_OK) return st;
     if (theta) *theta = out.theta;
     if (iterations) *iterations = out.iters;
     if (!out.converged) return fail(h, SPMPS_ERR_NOT_CONVERGED, "Davidson reached its iteration cap");
@@ -897,6 +931,8 @@ spmps_status spmps_sweep(spmps_handle h, int n_sweeps, double* energies) {
                 st = update_right(h, k + 1);
                 h->center = k;
             }
+            if (st != SPMPS_OK) return st;
+            st = excited_after_step(h, k, mr);
             if (st != SPMPS_OK) return st;
         }
         if (energies) energies[sw] = theta;

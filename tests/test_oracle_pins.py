@@ -680,3 +680,55 @@ def test_screened_action_reduces_to_the_action_and_error_shrinks_with_tau():
         y, z = P.apply(x, k, screen=tau)
         errs.append(np.abs(y - y0).max() / np.abs(y0).max())
     assert 0.0 < errs[0] < errs[1] < errs[2]
+
+
+# ---- state-specific excited states (Sec. 2.3.2, Eq. orthoB) -----------------------------------
+
+def _projected_overlap_fock(mps0, mps1, K, twoS, twoM, ng):
+    beta, c = Q.projector_quadrature(twoS, twoM, ng)
+    p0, p1 = S.to_full_vector(mps0), S.to_full_vector(mps1)
+    pp = sum(cg * fock.apply_site_ops(p1, [Q.site_rotation(b)] * K) for b, cg in zip(beta, c))
+    return float(p0 @ pp)
+
+
+@pytest.mark.parametrize("K,N,twoM,twoS,D,k", [(5, 5, 1, 1, 8, 1), (6, 6, 0, 0, 12, 2), (6, 6, 0, 2, 10, 0)])
+def test_b_vector_gives_the_projected_overlap(K, N, twoM, twoS, D, k):
+    """B . x = <Psi_0| P |Psi_1> (Eq. orthoB), against the overlap of the full Fock vectors with the
+    many-body projector applied, for two unrelated random MPS (no canonical form needed)."""
+    from oracle import excited as X
+    ng = Q.n_exact(K, N, twoM, twoS)
+    l0, t0 = inputs.random_mps(K, N, twoM, D, 11)
+    l1, t1 = inputs.random_mps(K, N, twoM, D, 12)
+    m0 = S.MPS([q.copy() for q in l0], [t.copy() for t in t0], 0)
+    m1 = S.MPS([q.copy() for q in l1], [t.copy() for t in t1], 0)
+    ov = X.Overlap(m0, m1, twoS, twoM, ng)
+    ov.build(k)
+    x1 = np.einsum("asc,cjb->asjb", m1.A[k], m1.A[k + 1])
+    val = float(np.vdot(ov.B(k), x1))
+    ref = _projected_overlap_fock(m0, m1, K, twoS, twoM, ng)
+    assert abs(val - ref) < 1e-12 * max(1.0, abs(ref)), (val, ref)
+    assert abs(ref) > 1e-6  # the two states do overlap, so the check is not vacuous
+
+
+def test_excited_sweeps_reach_the_second_spin_state():
+    """K=6 Hubbard chain at half filling, S=0, D=64 (untruncated): after the ground state, the
+    constrained sweeps reach the second-lowest singlet of exact diagonalisation, orthogonal to
+    the ground state in the projected metric."""
+    from oracle import excited as X
+    K, N, twoM, twoS, D = 6, 6, 0, 0, 64
+    ng = Q.n_exact(K, N, twoM, twoS)
+    h1, eri = inputs.hubbard_chain(K, 1.0, 4.0)
+    Na, Nb = inputs.electron_counts(N, twoM)
+    H, _ = fock.hamiltonian(K, Na, Nb, h1, eri)
+    S2 = fock.s_squared(K, Na, Nb).toarray()
+    w = np.linalg.eigvalsh(H.toarray() + 50.0 * S2 @ S2)
+    l0, t0 = inputs.random_mps(K, N, twoM, D, 1)
+    P0 = S.prepare(l0, t0, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, ng)
+    S.run_sweeps(P0, D, 3, tol_r=1e-9, max_iter=300)
+    l1, t1 = inputs.random_mps(K, N, twoM, D, 7)
+    P1 = S.prepare(l1, t1, M.hubbard_mpo(K, 1.0, 4.0), twoS, twoM, ng)
+    ov = X.Overlap(P0.mps, P1.mps, twoS, twoM, ng)
+    ov.build(0)
+    log = X.run_excited_sweeps(P1, [ov], D, 3, tol_r=1e-9, max_iter=300)
+    assert abs(log.sweep_energy[-1] - w[1]) < 1e-9, (log.sweep_energy, w[:3])
+    assert abs(_projected_overlap_fock(P0.mps, P1.mps, K, twoS, twoM, ng)) < 1e-9
