@@ -105,6 +105,17 @@ typedef struct {
                            such sub-block of the channel are dropped from phases A and C.  An
                            approximation: y and z change by amounts of the order of m_screen;
                            spmps_apply_flops reports the reduced work. */
+    int fp64_tensor_cores; /* 1: the FP64 block products of phases A and C of every projected action
+                           (H and N, both whenever they are computed in FP64) run on the tensor
+                           cores as exact products of 8-bit digits: per K stage of 32, each entry
+                           is cut into seven signed base-256 digits against the exponent of its row
+                           (A) or column (B) maximum, the digit products of each level p + q = 2..9
+                           are summed exactly in an FP32 tensor-memory accumulator by
+                           tcgen05.mma kind::f16 (every partial sum an integer below 2^24), and the
+                           levels are combined in FP64 (the splitting scheme of Ozaki, Ogita, Oishi
+                           and Rump, Numer. Algorithms 59, 2012).  The error per stage is of the
+                           order of 32 * 2^-55 max|a_i.| max|b_.j|, the size of FP64 rounding;
+                           0 (default): the FP64 pipe. */
 } spmps_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -340,8 +351,9 @@ spmps_status spmps_profile(spmps_handle h, int enable);
  * uploading contraction plans (ms of host clock, launches = plans built), 6 = assembly and
  * factorisation of the metric blocks (precond 4, once per two-site step), 7 = the per-iteration
  * solves with them, 8 = the reduced-precision block-GEMM launches (TF32 / 3xTF32 H products;
- * kind 0 then counts the FP64 ones only).  Synchronises the
- * handle's stream. */
+ * kind 0 then counts the FP64 ones only), 9 = the FP64-accurate split-product GEMM launches
+ * (fp64_tensor_cores; kind 0 then counts only the block products outside projected actions).
+ * Synchronises the handle's stream. */
 spmps_status spmps_kernel_stats(spmps_handle h, int kind, int64_t* launches, double* ms, double* flops);
 
 /* ---- Learned Davidson correction (no counterpart in the paper) ------------------------------

@@ -40,7 +40,7 @@ class Options(C.Structure):
         ("dav_max_sub", C.c_int), ("dav_max_iter", C.c_int), ("device", C.c_int),
         ("jacobi_smem_max", C.c_int), ("precision", C.c_int), ("autotune", C.c_int),
         ("metric_max_dim", C.c_int), ("tc_wait_polls", C.c_int), ("tensor_core_kernel", C.c_int),
-        ("m_screen", C.c_double),
+        ("m_screen", C.c_double), ("fp64_tensor_cores", C.c_int),
     ]
 
 
@@ -129,7 +129,7 @@ class Spmps:
     def __init__(self, K, N, twoM, twoS, n_beta, D, *, batched=True, precond="diag", cg_steps=5,
                  dav_tol_r=1e-6, dav_tol_theta=1e-10, dav_max_sub=20, dav_max_iter=200, device=0,
                  jacobi_smem_max=0, precision="fp64", autotune=False, metric_max_dim=0,
-                 tc_wait_polls=0, tensor_core_kernel="tcgen05", m_screen=0.0):
+                 tc_wait_polls=0, tensor_core_kernel="tcgen05", m_screen=0.0, fp64_tensor_cores=False):
         self.lib = load_library()
         o = Options()
         self.lib.spmps_default_options(C.byref(o))
@@ -144,6 +144,7 @@ class Spmps:
         o.tc_wait_polls = tc_wait_polls
         o.tensor_core_kernel = {"tcgen05": 0, "mma_sync": 1}[tensor_core_kernel]
         o.m_screen = m_screen
+        o.fp64_tensor_cores = 1 if fp64_tensor_cores else 0
         h = C.c_void_p()
         self._h = None
         self._check(self.lib.spmps_create(K, N, twoM, twoS, n_beta, D, C.byref(o), C.byref(h)), None)

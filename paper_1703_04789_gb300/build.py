@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libspmps.so")
-SOURCES = ["host.cpp", "mpo_ab_initio.cpp", "kernels.cu", "engine.cu", "sweep.cu", "metric.cu", "noalloc.cu", "mlp.cu", "learned.cu", "tf32.cu", "state_io.cu", "properties.cu", "peaks.cu", "tc_gemm.cu", "screen.cu", "excited.cu"]
+SOURCES = ["host.cpp", "mpo_ab_initio.cpp", "kernels.cu", "engine.cu", "sweep.cu", "metric.cu", "noalloc.cu", "mlp.cu", "learned.cu", "tf32.cu", "state_io.cu", "properties.cu", "peaks.cu", "tc_gemm.cu", "ozaki.cu", "screen.cu", "excited.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -282,6 +282,30 @@ spmps_status plan_upload(spmps_t* h, Plan& P) {
             P.stA.ok = P.stC.ok = false;
         }
     }
+    // stacks of every (op, g) range for the FP64-accurate split-product GEMM; its status word is
+    // allocated here so that running the plan allocates nothing
+    P.ozA.clear();
+    P.ozC.clear();
+    if (P.reduce_nx > 0 && h->opt.fp64_tensor_cores && a_task_rng.size() > 1 && c_task_rng.size() > 1) {
+        const bool okA = build_tc_plan(P.A, a_task_rng, static_cast<int>(a_task_rng.size()) - 1, gemm_oz_columns(), P.ozA);
+        const bool okC = build_tc_plan(P.C, c_task_rng, static_cast<int>(c_task_rng.size()) - 1, gemm_oz_columns(), P.ozC);
+        if (okA && okC) {
+            for (TcPlan* T : {&P.ozA, &P.ozC}) {
+                DevMem* d = T == &P.ozA ? P.d_ozA : P.d_ozC;
+                CK(upload(d[0], T->stacks, h->stream));
+                CK(upload(d[1], T->rows, h->stream));
+                CK(upload(d[2], T->segs, h->stream));
+                CK(upload(d[3], T->atab, h->stream));
+                CK(upload(d[4], T->units, h->stream));
+            }
+            if (!h->tc_err.p) {
+                CK(h->tc_err.ensure(sizeof(int)));
+                CK(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream));
+            }
+        } else {
+            P.ozA.ok = P.ozC.ok = false;
+        }
+    }
     CK(h->work1.ensure(std::max<int64_t>(1, P.t1_size) * sizeof(double)));
     CK(h->work2.ensure(std::max<int64_t>(1, P.t2_size) * sizeof(double)));
     CK(cudaStreamSynchronize(h->stream));
@@ -312,6 +336,19 @@ spmps_status plan_run(spmps_t* h, Plan& P, Slots S, int r0, int r1, cudaStream_t
                     const std::vector<int>& tc_rng, int a, int b) -> cudaError_t {
         auto one = [&](int lo, int hi, int tf) -> cudaError_t {
             if (hi <= lo) return cudaSuccess;
+            const TcPlan& OZ = &tasks == &P.d_tasksA ? P.ozA : P.ozC;
+            if (!tf && OZ.ok && h->opt.fp64_tensor_cores && h->tc_err.p) {
+                // FP64-accurate split products on the tensor cores over the units of [lo, hi)
+                const DevMem* d = &tasks == &P.d_tasksA ? P.d_ozA : P.d_ozC;
+                ++h->launches;
+                const int rec = h->profile ? prof_begin(h, st, 9, range_flops(fl, lo, hi)) : -1;
+                const cudaError_t e2 = launch_gemm_oz(S, d[0].as<TcStack>(), d[1].as<TcRow>(), d[2].as<TcSeg>(),
+                                                      d[3].as<uint64_t>(), cmaps.as<int>(), d[4].as<int4>(),
+                                                      OZ.unit_rng[lo], OZ.unit_rng[hi], h->tc_err.as<int>(),
+                                                      h->opt.tc_wait_polls, st);
+                if (rec >= 0) prof_end(h, st, rec);
+                return e2;
+            }
             const TcPlan& TP = &tasks == &P.d_tasksA ? P.stA : P.stC;
             if (tf && split && TP.ok && h->opt.tensor_core_kernel == 0 && hi <= G) {
                 // stacked tcgen05 GEMM over the units of the H-part ranges [lo, hi)
@@ -1451,6 +1488,7 @@ void spmps_default_options(spmps_options* o) {
     o->tc_wait_polls = 0;
     o->tensor_core_kernel = 0;
     o->m_screen = 0.0;
+    o->fp64_tensor_cores = 0;
 }
 
 const char* spmps_last_error(spmps_handle h) { return h ? h->err.c_str() : g_static_err.c_str(); }
@@ -1474,6 +1512,8 @@ spmps_status spmps_create(int K, int N, int twoM, int twoS, int n_beta, int D, c
     if (!(o.m_screen >= 0.0 && o.m_screen < 1.0)) return fail(nullptr, SPMPS_ERR_BAD_INPUT, "m_screen must be in [0, 1)");
     if (o.tensor_core_kernel < 0 || o.tensor_core_kernel > 1)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "tensor_core_kernel must be 0 or 1");
+    if (o.fp64_tensor_cores < 0 || o.fp64_tensor_cores > 1)
+        return fail(nullptr, SPMPS_ERR_BAD_INPUT, "fp64_tensor_cores must be 0 or 1");
     if (o.metric_max_dim < 0 || o.tc_wait_polls < 0)
         return fail(nullptr, SPMPS_ERR_BAD_INPUT, "metric_max_dim and tc_wait_polls must be >= 0");
     if (o.jacobi_smem_max < 0 || o.jacobi_smem_max > 112)

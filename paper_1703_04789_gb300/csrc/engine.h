@@ -116,6 +116,8 @@ struct Plan {
     std::vector<int> tcA_rng, tcC_rng;       // their ranges per (op, g)
     TcPlan stA, stC;                         // tcgen05 stacks of the H part, phases A and C
     DevMem d_stA[5], d_stC[5];               // their stacks, rows, segments, A table, units
+    TcPlan ozA, ozC;                         // stacks of all (op, g) ranges for the FP64-accurate
+    DevMem d_ozA[5], d_ozC[5];               // split-product GEMM (fp64_tensor_cores)
     // diagonal (apply plans only)
     std::vector<DiagBlock> diag_blocks;
     std::vector<DiagTerm> diag_terms;
@@ -199,9 +201,9 @@ struct spmps_t {
     };
     bool profile = false;
     std::vector<TimerRec> timers_live, timers_free;
-    static constexpr int kProfKinds = 9;
-    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    static constexpr int kProfKinds = 10;
+    int64_t prof_launches[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, prof_flops[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace spmps {

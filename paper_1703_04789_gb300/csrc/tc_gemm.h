@@ -63,4 +63,16 @@ cudaError_t launch_gemm_tc(const Slots& slots, const SlotsF& split, const TcStac
                            const TcSeg* segs, const uint64_t* atab, const int* cmaps, const int4* units, int u0,
                            int u1, int nt, int split3, int* err, int wait_polls, cudaStream_t st);
 
+// FP64-accurate variant over the same stacks (tiles of 128 rows x gemm_oz_columns() columns, so the
+// plan must be built with nt = gemm_oz_columns()): A and B read in FP64, every K stage of 32 split
+// into seven signed 8-bit digits per entry against per-row and per-column exponents, the digit
+// products summed exactly by tcgen05.mma kind::f16 (FP16 digits, FP32 accumulators in tensor
+// memory, one per level p + q = 2 .. 9, every partial sum an integer below 2^24) and combined in
+// FP64 (the splitting scheme of Ozaki, Ogita, Oishi and Rump).  Error per stage of the order of
+// 32 * 2^-55 max|a_i.| max|b_.j|.  err[0] and wait_polls as for launch_gemm_tc.
+cudaError_t launch_gemm_oz(const Slots& slots, const TcStack* stacks, const TcRow* rows, const TcSeg* segs,
+                           const uint64_t* atab, const int* cmaps, const int4* units, int u0, int u1, int* err,
+                           int wait_polls, cudaStream_t st);
+int gemm_oz_columns();
+
 }  // namespace spmps

@@ -36,12 +36,14 @@ def hubbard_chain_handles(warm_sweeps: int, spec=HUBBARD_L24, targets=None, **op
 AB_INITIO_K20 = {"K": 20, "N": 30, "twoM": 10, "twoS": 10, "n_beta": 12, "seed": 3}
 
 
-def ab_initio_action(D: int, spec=AB_INITIO_K20, precisions=("fp64", "3xtf32"), site=None, m_screen=0.0):
+def ab_initio_action(D: int, spec=AB_INITIO_K20, precisions=("fp64", "3xtf32", "fp64_tc"), site=None, m_screen=0.0):
     """One projected action at the middle of the synthetic active-space workload (K=20, N=30,
     2M=2S=10, n_beta=12; integrals from inputs.synthetic_active_space) for a seeded random MPS of
     bond dimension D, canonicalised on the GPU: per precision form the phase times (CUDA events),
     the algorithmic flops and bytes, the error of y against the FP64 action, and the device memory
-    in use (environments of every bond, the action's intermediates)."""
+    in use (environments of every bond, the action's intermediates).  Form "fp64_tc" is the FP64
+    action with its block products of phases A and C split into exact digit products on the
+    tensor cores (fp64_tensor_cores)."""
     import torch
     from . import Spmps, inputs
     K, N, twoM, twoS, G = spec["K"], spec["N"], spec["twoM"], spec["twoS"], spec["n_beta"]
@@ -52,7 +54,8 @@ def ab_initio_action(D: int, spec=AB_INITIO_K20, precisions=("fp64", "3xtf32"), 
            "forms": {}}
     y64 = None
     for prec in precisions:
-        dev = Spmps(K, N, twoM, twoS, G, D, precision=prec, autotune=False, m_screen=m_screen)
+        dev = Spmps(K, N, twoM, twoS, G, D, precision="fp64" if prec == "fp64_tc" else prec, autotune=False,
+                    m_screen=m_screen, fp64_tensor_cores=prec == "fp64_tc")
         dev.set_hamiltonian(h1, eri, ecore)
         dev.set_mps(labels, tens, center=0)
         dev.canonicalize()
@@ -86,6 +89,8 @@ def main():
     ap.add_argument("--profile-sweep", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "3xtf32"])
+    ap.add_argument("--fp64-tensor-cores", action="store_true",
+                    help="FP64 block products of the action as exact digit products on the tensor cores")
     args = ap.parse_args()
     import torch
     from . import build
@@ -95,7 +100,8 @@ def main():
         for D in args.ab_initio_D:
             print(json.dumps(ab_initio_action(D)), flush=True)
         return
-    h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune, precision=args.precision)[0]
+    h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune, precision=args.precision,
+                              fp64_tensor_cores=args.fp64_tensor_cores)[0]
     dev = h["dev"]
     lay = dev.x_layout(args.site)
     x = torch.tensor(np.random.default_rng(0).standard_normal(lay["n_x"]), device="cuda")
