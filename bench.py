@@ -43,9 +43,12 @@ METRIC = "SP-MPS sweep time & projected H_eff·x TFLOP/s vs FP64 plain at 1e-6 E
 # Projected actions per sweep of the FP64 plain form on this workload (measured on GB300, mean of
 # the two targets); scales the oracle's per-action time to a sweep for --impl reference.
 ACTIONS_PER_PLAIN_SWEEP = 5745
-# DRAM bytes per k_gemm_f64 launch of the middle-site action (phase A 63.1 MB, phase C 113.5 MB,
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel)
-TRAFFIC_PER_LAUNCH = 88.3e6
+# DRAM bytes per k_gemm_oz launch of the middle-site FP64 action (phase A 74.7 MB, phase C 136.0 MB,
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel, Hubbard L=24, D=256, sites
+# (11, 12) after one warm-up sweep)
+TRAFFIC_PER_LAUNCH = 105.3e6
+# FP16 digit products per FP64 multiply-add in the split-product GEMM (levels 2..9 of 7 x 7 digits)
+DIGIT_PRODUCTS = 34
 WORKLOAD = {
     "workload": "Hubbard chain L=24 open, t=1, U=4, N=24, targets (2M,2S)=(0,0) and (2,2), D=256, "
                 "n_beta=8; step = one two-site sweep per target from a checkpoint taken after the warm-up sweeps",
@@ -54,10 +57,13 @@ WORKLOAD = {
     "davidson": "|r| < 1e-6 and |dtheta| < 1e-10, subspace 20, cap 200",
     "forms": {"fast": "grouped launches over all beta points and blocks, autotuned GEMM tiles, H part of the "
                       "block products in 3xTF32 on the tensor cores (stacked tcgen05 GEMM) until |r| < 1e-5, then "
-                      "FP64; diagonal correction",
-              "fast_mma_sync": "fast with the warp-level mma.sync tensor-core kernel",
+                      "FP64; every FP64 block product of the action (N_eff x, the FP64 finish) as exact 8-bit digit "
+                      "products on the tensor cores (split-product GEMM, FP64-accurate); diagonal correction",
+              "fast_fp64_tc": "fast with every block product of the action FP64-accurate on the split-product GEMM "
+                              "(no 3xTF32 stage)",
+              "fast_fp64": "fast with every block product in FP64 on the FP64 pipe (no tensor cores)",
+              "fast_mma_sync": "fast with the warp-level mma.sync kernel for the 3xTF32 stage",
               "fp64_plain": "one launch per beta point and phase, fixed tiles, FP64, diagonal correction",
-              "fast_fp64": "fast with every block product in FP64",
               "fast_learned": "fast with the learned Davidson correction"},
     "l2": "flushed before every timed sweep (256 MiB write); environments of all bonds exceed L2",
 }
@@ -179,12 +185,13 @@ def _time_sweeps(dev, ckpt, steps, flush, torch):
 
 
 FORMS = {
-    "fast": dict(batched=True, autotune=True, precision="3xtf32", precond="diag"),
+    "fast": dict(batched=True, autotune=True, precision="3xtf32", precond="diag", fp64_tensor_cores=True),
     "fp64_plain": dict(batched=False, autotune=False, precision="fp64", precond="diag"),
+    "fast_fp64_tc": dict(batched=True, autotune=True, precision="fp64", precond="diag", fp64_tensor_cores=True),
     "fast_fp64": dict(batched=True, autotune=True, precision="fp64", precond="diag"),
-    "fast_learned": dict(batched=True, autotune=True, precision="3xtf32", precond="learned"),
+    "fast_learned": dict(batched=True, autotune=True, precision="3xtf32", precond="learned", fp64_tensor_cores=True),
     "fast_mma_sync": dict(batched=True, autotune=True, precision="3xtf32", precond="diag",
-                          tensor_core_kernel="mma_sync"),
+                          tensor_core_kernel="mma_sync", fp64_tensor_cores=True),
 }
 
 
@@ -232,7 +239,7 @@ def run_ours(args):
 
     # kernel breakdown from a separate, untimed sweep of the S=0 target with the per-launch profiler
     names = ["gemm_fp64", "comb", "ritz", "davidson_vector_ops", "decimation_eigen", "host_planning",
-             "metric_factor", "metric_solve", "gemm_tensor_core"]
+             "metric_factor", "metric_solve", "gemm_tensor_core", "gemm_fp64_split"]
     fast[0].profile(True)
     prof_run = _time_sweeps(fast[0], hs[0]["ckpt"], 1, flush, torch)
     breakdown = {}
@@ -250,8 +257,9 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) * 1e3, "cuda") * 1e-3
     e2e_value = len(hs) * world / e2e_s
     # the block GEMMs at the middle site of the S=0 target, from the fast form's checkpointed MPS:
-    # phases A and C of the H part alone (the fast form's tensor-core products, y only) and of the
-    # whole FP64 action (CUDA events on the handle's stream, warm, mean of 5)
+    # phases A and C of the H part alone (the fast form's 3xTF32 products, y only) and of the whole
+    # FP64-accurate action (y and z) on the split-product GEMM and on the FP64 pipe (CUDA events on
+    # the handle's stream, warm, mean of 5)
     site = WORKLOAD["site"]
 
     def middle_site_phases(dev, with_z):
@@ -270,6 +278,10 @@ def run_ours(args):
     dtc.set_mps(*hs[0]["ckpt"][:2], center=hs[0]["ckpt"][2])
     phase_tc, (fl_op, by_op) = middle_site_phases(dtc, with_z=False)
     dtc.close()
+    doz = _handle("fast_fp64_tc", hs[0]["twoM"], hs[0]["twoS"])
+    doz.set_mps(*hs[0]["ckpt"][:2], center=hs[0]["ckpt"][2])
+    phase_oz, _ = middle_site_phases(doz, with_z=True)
+    doz.close()
     d64 = _handle("fast_fp64", hs[0]["twoM"], hs[0]["twoS"])
     d64.set_mps(*hs[0]["ckpt"][:2], center=hs[0]["ckpt"][2])
     phase, _ = middle_site_phases(d64, with_z=True)
@@ -283,7 +295,7 @@ def run_ours(args):
         res_plain.append(_time_sweeps(d, h["ckpt"], 1, flush, torch))
         d.close()
     variants = {}
-    for form in ("fast_fp64", "fast_mma_sync", "fast_learned"):
+    for form in ("fast_fp64_tc", "fast_fp64", "fast_mma_sync", "fast_learned"):
         d = _handle(form, hs[0]["twoM"], hs[0]["twoS"], params)
         r = _time_sweeps(d, hs[0]["ckpt"], 1, flush, torch)
         d.close()
@@ -303,7 +315,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 6), "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (H block products 3xTF32 until |r| < 1e-5, FP64 finish)", "data": "synthetic",
+        "dtype": "f64 (H block products 3xTF32 until |r| < 1e-5, then FP64-accurate split products)", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
         "sweep_s": {"fast": {k: round(v, 4) for k, v in fast_mean.items()},
                     "fp64_plain": {k: round(v, 4) for k, v in plain_s.items()}},
@@ -317,7 +329,8 @@ def run_ours(args):
         "variants_2S=0": variants,
         "learned_correction": mlp_info,
         "apply_tflops": round(apply_flops / (total_ms * 1e-3) / 1e12, 6),
-        "roofline": _roofline(phase_tc, phase, fl_op, by_op, hbm, tf32_peaks, peak, breakdown),
+        "roofline": _roofline(phase_oz, phase_tc, phase, fl_op, by_op, hbm, tf32_peaks, peak, breakdown,
+                              _measured_peaks().get("bf16_tflops")),
         "time_breakdown_ms": dict(breakdown, timed_sweeps_total_ms=round(total_ms, 2)),
         "e2e": {"value": round(e2e_value, 6), "unit": "sweeps/s", "h2d_bytes_per_step": sum(h["ckpt_bytes"] for h in hs),
                 "d2h_bytes_per_step": 8 * len(hs)},
@@ -339,37 +352,56 @@ def _measured_peaks():
         return {}
 
 
-def _roofline(phase_tc, phase64, fl_op, by_op, hbm, tf32_peaks, fp64_peak, breakdown):
-    """Roofline of the fast form's dominant kernel and of its tensor-core kernel.
+def _roofline(phase_oz, phase_tc, phase64, fl_op, by_op, hbm, tf32_peaks, fp64_peak, breakdown, f16_peak):
+    """Roofline of the fast form's dominant kernel and of its other block-GEMM kernels.
 
-    The kernel breakdown of a fast sweep (separate profiled pass) puts the FP64 block GEMMs first:
-    the N_eff products, the FP64 finish of every Davidson solve, the environment updates and the
-    decimation density matrices all run in k_gemm_f64, which is bound by the FP64 pipe
-    ("alu": achieved = algorithmic flops of phases A and C of the middle-site FP64 action / their
-    CUDA-event time, against the FP64 FMA peak measured on all SMs).  The tensor-core products of
-    the H part (stacked tcgen05 GEMM, k_gemm_tc) are reported beside it against the measured HBM
-    copy bandwidth (their reductions are 5 to a few hundred long: far below the tensor pipe's
-    ridge point) and against the measured tcgen05 kind::tf32 peak."""
-    t64 = (phase64[1] + phase64[3]) * 1e-3
+    The kernel breakdown of a fast sweep (separate profiled pass) puts the split-product GEMM first
+    (k_gemm_oz: every FP64-accurate block product of phases A and C, H and N).  Its arithmetic is
+    FP16 tensor-core MMAs, DIGIT_PRODUCTS digit products per FP64 multiply-add, so its roofline is
+    the FP16 dense tensor peak (the measured BF16 burst; FP16 has the same nominal dense rate):
+    achieved = DIGIT_PRODUCTS x the algorithmic FP64 flops of phases A and C of the middle-site action
+    / their CUDA-event time.  Beside it, the same algorithmic FP64 flops per second against the
+    measured FP64 pipe (what an FP64 GEMM could reach), the FP64 pipe kernel on the same action, and
+    the 3xTF32 products of the H part (k_gemm_tc) against the HBM bandwidth and the tcgen05
+    kind::tf32 peak."""
     flops64 = float(fl_op[0][0] + fl_op[0][2] + fl_op[1][0] + fl_op[1][2])
+    t_oz = (phase_oz[1] + phase_oz[3]) * 1e-3
+    t64 = (phase64[1] + phase64[3]) * 1e-3
     t_tc = (phase_tc[1] + phase_tc[3]) * 1e-3
     bytes_tc = float(by_op[0][0] + by_op[0][2])
     flops_tc = float(fl_op[0][0] + fl_op[0][2])
     peak_bw = hbm if hbm else 6800.0
+    peak16 = f16_peak if f16_peak else 1900.0
+    goz = breakdown.get("gemm_fp64_split", {})
     g64 = breakdown.get("gemm_fp64", {})
     gtc = breakdown.get("gemm_tensor_core", {})
     total = breakdown.get("profiled_sweep_ms") or 0.0
+    ach_oz = DIGIT_PRODUCTS * flops64 / t_oz / 1e12
+    fp64_eq = flops64 / t_oz / 1e12
     ach64 = flops64 / t64 / 1e12
     return {
-        "bound": "alu", "kernel": "k_gemm_f64: phases A and C of the FP64 projected action (H and N) at sites (11, 12), S=0",
-        "achieved": round(ach64, 6), "peak": round(fp64_peak, 6), "unit": "TFLOP/s",
-        "frac": round(ach64 / fp64_peak, 4) if fp64_peak else None,
-        "peak_source": "measured: FP64 FMA-chain kernel on all SMs (spmps_device_fp64_peak; nominal 1.25)",
+        "bound": "tensor",
+        "kernel": "k_gemm_oz: FP64-accurate split-product GEMM (tcgen05 kind::f16 on 8-bit digits), phases A and C "
+                  "of the projected action (H and N) at sites (11, 12), S=0",
+        "achieved": round(ach_oz, 4), "peak": round(peak16, 1), "unit": "TFLOP/s",
+        "frac": round(ach_oz / peak16, 5),
+        "peak_source": ("measured cuBLAS BF16 burst (MEASURED_PEAKS.json bf16_tflops) as the FP16 dense peak "
+                        "(same nominal rate)") if f16_peak else "fallback 1.9 PFLOP/s",
+        "achieved_note": f"{DIGIT_PRODUCTS} FP16 digit products per algorithmic FP64 multiply-add",
         "traffic": TRAFFIC_PER_LAUNCH,
-        "traffic_note": "dram bytes read + written per k_gemm_f64 launch (mean of the phase-A and phase-C launches) "
+        "traffic_note": "dram bytes read + written per k_gemm_oz launch (mean of the phase-A and phase-C launches) "
                         "from one ncu capture of the middle-site action",
-        "phase_ms": [round(float(v), 4) for v in phase64],
-        "share_of_fast_sweep": round(g64.get("ms", 0.0) / total, 4) if total else None,
+        "phase_ms": [round(float(v), 4) for v in phase_oz],
+        "share_of_fast_sweep": round(goz.get("ms", 0.0) / total, 4) if total else None,
+        "fp64_equivalent": {"achieved_tflops": round(fp64_eq, 4), "fp64_pipe_peak_tflops": round(fp64_peak, 4),
+                            "frac_of_fp64_pipe": round(fp64_eq / fp64_peak, 4) if fp64_peak else None,
+                            "peak_source": "measured: FP64 FMA-chain kernel on all SMs (spmps_device_fp64_peak)"},
+        "fp64_pipe_kernel": {
+            "kernel": "k_gemm_f64 on the same action (the fast_fp64 form)", "bound": "alu",
+            "achieved_tflops": round(ach64, 4), "peak_tflops": round(fp64_peak, 4),
+            "frac": round(ach64 / fp64_peak, 4) if fp64_peak else None,
+            "phase_ms": [round(float(v), 4) for v in phase64],
+            "share_of_fast_sweep": round(g64.get("ms", 0.0) / total, 4) if total else None},
         "tensor_core_kernel": {
             "kernel": "k_gemm_tc: stacked tcgen05 kind::tf32 (3xTF32) H products of phases A and C, same site",
             "bound": "hbm", "achieved_GBs": round(bytes_tc / t_tc / 1e9, 2), "peak_GBs": round(peak_bw, 1),
