@@ -53,7 +53,9 @@ typedef struct {
     int batched;        /* 1: one grouped launch per contraction phase over all beta points and
                            blocks (default); 0: one launch per beta point and phase          */
     int precond;        /* Davidson correction: 0 = diagonal (default), 1 = metric CG,
-                           2 = learned (spmps_mlp_*; the diagonal correction is its fallback),
+                           2 = learned (spmps_mlp_*; the diagonal correction replaces it for the
+                           rest of a solve once |r| has not improved by 10 % in 12 iterations,
+                           and when its direction lies in the basis),
                            3 = Olsen: the diagonal correction plus eps M^-1 N x with eps making
                            it N-orthogonal to x (M = diag H - theta diag N),
                            4 = metric blocks: t = (N_eff + s I)^-1 r with s = 1e-7.  N_eff is the

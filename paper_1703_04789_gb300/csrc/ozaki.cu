@@ -141,6 +141,8 @@ __device__ __forceinline__ void pair_signs(const double v[NV], __half2 sg[NV / 2
 
 // One CTA of 256 threads per 128 x 32 tile: warp w serves tensor-memory lanes 32 (w mod 4) .. + 31
 // (tile rows) and the column half (K half while splitting) w / 4, so every row has two threads.
+// Two CTAs per SM (shared memory and tensor memory each allow two): one CTA's copies and digit
+// splitting overlap the other's MMAs and combination.
 __global__ void __launch_bounds__(kOzThreads, 2) k_gemm_oz(Slots S, const TcStack* __restrict__ stacks,
                                                           const TcRow* __restrict__ rows, const TcSeg* __restrict__ segs,
                                                           const uint64_t* __restrict__ atab, const int* __restrict__ cmaps,
@@ -347,12 +349,15 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_gemm_oz(Slots S, const TcStac
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                long long T = 0;
+                int iv[kLevels];
 #pragma unroll
-                for (int L = 0; L < 6; ++L)
-                    T += static_cast<long long>(__float2int_rz(__uint_as_float(v[L][j]))) * (1ll << (40 - 8 * L));
-                T += static_cast<long long>(__float2int_rz(__uint_as_float(v[6][j])) >> 8);
-                T += static_cast<long long>(__float2int_rz(__uint_as_float(v[7][j])) >> 16);
+                for (int L = 0; L < kLevels; ++L) iv[L] = __float2int_rz(__uint_as_float(v[L][j]));
+                // T = sum_l v_l 2^(56 - 8l): levels 2-3 and 4-5 paired in 32 bits (below 2^30 and
+                // 2^31), the rest in one 64-bit multiply-add
+                const int a = iv[0] * 256 + iv[1];
+                const int bb = iv[2] * 256 + iv[3];
+                const long long c = static_cast<long long>(iv[4]) * 256 + (iv[5] + (iv[6] >> 8) + (iv[7] >> 16));
+                const long long T = static_cast<long long>(bb) * 65536 + c + static_cast<long long>(a) * 4294967296ll;
                 const int fe = Er + colE[16 * h + cb + j] - 1077;  // biased exponent of the unit 2^(e_i + e_j - 56)
                 const double unit = fe > 0 && fe < 2047 ? __longlong_as_double(static_cast<long long>(fe) << 52) : 0.0;
                 acc[cb + j] = fma(static_cast<double>(T), unit, acc[cb + j]);

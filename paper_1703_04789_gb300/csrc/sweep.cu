@@ -248,6 +248,9 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
     }
     const bool learned = h->opt.precond == 2 && ML.ready;
     if (learned) CK(ML.err.ensure(sizeof(int)));
+    // the learned correction is used until |r| stops improving by 10 % for kStagnation iterations;
+    // the solve then continues with the diagonal correction
+    bool learned_on = learned;
     auto finish_harvest = [&]() -> spmps_status {
         if (!harvest || stored == 0) return SPMPS_OK;
         const int64_t room = ML.capacity - ML.count;
@@ -316,7 +319,7 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
             CK(launch_axpy_ratio(B.t.as<double>(), B.cg_ap.as<double>(), n, sc + 11, sc + 12, -1.0, h->stream));
             h->launches += 6;
         }
-        if (harvest || learned) {
+        if (harvest || learned_on) {
             // |d|^2 of the diagonal correction (sc[7]) for the features
             CK(launch_norm2(B.t.as<double>(), n, sc + 7, h->partial.as<double>(), h->stream));
             h->launches += 2;
@@ -332,7 +335,7 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
             ++stored;
         }
         const double* tsrc = B.t.as<double>();  // the correction to append: diagonal, CG, or learned
-        if (learned) {
+        if (learned_on) {
             CK(cudaMemsetAsync(ML.err.p, 0, sizeof(int), h->stream));
             CK(mlp::infer_tc(B.r.as<double>(), B.t.as<double>(), B.dh.as<double>(), B.dn.as<double>(), sc, sc + 2,
                              sc + 7, n, ML.w2core.as<__nv_bfloat16>(), ML.params.as<float>(), B.cg_p.as<double>(),
@@ -381,7 +384,8 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         // one host read per iteration: theta, kept metric directions, |r|^2, |t|^2
         CK(cudaMemcpyAsync(host, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         int infer_err = 0, tc_err = 0;
-        if (learned) CK(cudaMemcpyAsync(&infer_err, ML.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        const bool inferred = learned_on;  // whether this iteration's correction came from the network
+        if (inferred) CK(cudaMemcpyAsync(&infer_err, ML.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         if (h->tc_err.p) CK(cudaMemcpyAsync(&tc_err, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         ++h->dav_iters;
@@ -406,6 +410,7 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         // plain TF32 (precision 1) has a noise floor near its switch tolerance: switch on stagnation
         // too; 3xTF32 reaches its tolerance well above its floor
         const bool stagnated = h->apply_precision == 1 && it - best_it >= kStagnation;
+        if (learned_on && it - best_it >= kStagnation) learned_on = false;
         // and every solve finishes in FP64: switch at half the iteration cap at the latest
         // the error of the reduced-precision products grows with the scale of H: the switch level
         // is relative to |theta| (about 1e-6 for 3xTF32 and 1e-3 for TF32) where that is above
@@ -420,7 +425,7 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
             // the correction lies in the basis: fall back to the diagonal correction (after a
             // learned one), then to the residual itself
             double nrm2 = 0.0;
-            if (learned) {
+            if (inferred) {
                 CK(cudaMemcpyAsync(tcol, B.t.as<double>(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
                 st = orthogonalise(h, B, n, m, tcol, &nrm2);
                 if (st != SPMPS_OK) return st;

@@ -79,10 +79,64 @@ def ab_initio_action(D: int, spec=AB_INITIO_K20, precisions=("fp64", "3xtf32", "
     return out
 
 
+def ab_initio_step(D: int, spec=AB_INITIO_K20, forms=("fp64", "3xtf32_tc", "fp64_tc"), site=None, max_iter=200):
+    """One two-site optimisation step (Davidson to |r| < 1e-6 and decimation to D) at the middle of
+    the synthetic active-space workload, from the same canonicalised random MPS, per form: wall
+    time of the step (environments of the site built before it), Davidson iterations and theta,
+    with |theta - theta_fp64|.  Forms: "fp64" (FP64 pipe), "fp64_tc" (every block product of
+    phases A and C FP64-accurate on the split-product GEMM), "3xtf32_tc" (3xTF32 H products until
+    |r| < 1e-5, FP64-accurate split products otherwise)."""
+    import time
+    import torch
+    from . import Spmps, inputs
+    K, N, twoM, twoS, G = spec["K"], spec["N"], spec["twoM"], spec["twoS"], spec["n_beta"]
+    h1, eri, ecore = inputs.synthetic_active_space(K, spec["seed"])
+    labels, tens = inputs.random_mps(K, N, twoM, D, spec["seed"])
+    k = K // 2 - 1 if site is None else site
+    out = {"K": K, "N": N, "twoM": twoM, "twoS": twoS, "n_beta": G, "D": D, "site": k, "steps": {}}
+    opts = {"fp64": dict(precision="fp64"), "fp64_tc": dict(precision="fp64", fp64_tensor_cores=True),
+            "3xtf32_tc": dict(precision="3xtf32", fp64_tensor_cores=True)}
+    # canonical form with the centre on site k: canonicalise, then steps 0 .. k-1 with one Davidson
+    # iteration each (the Ritz vector of a one-vector basis is the current two-site tensor, so the
+    # decimation only moves the gauge)
+    g = Spmps(K, N, twoM, twoS, G, D, dav_max_iter=1, fp64_tensor_cores=True)
+    g.set_hamiltonian(h1, eri, ecore)
+    g.set_mps(labels, tens, center=0)
+    g.canonicalize()
+    for j in range(k):
+        g.optimize_step(j, True, allow_not_converged=True)
+    ck = g.get_mps()
+    g.close()
+    th64 = None
+    for form in forms:
+        dev = Spmps(K, N, twoM, twoS, G, D, dav_max_iter=max_iter, **opts[form])
+        dev.set_hamiltonian(h1, eri, ecore)
+        dev.set_mps(*ck[:2], center=ck[2])
+        lay = dev.x_layout(k)
+        x = torch.zeros(lay["n_x"], dtype=torch.float64, device="cuda")
+        dev.apply_heff(k, x, torch.empty_like(x), torch.empty_like(x))  # environments and plan of the site
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        th, it = dev.optimize_step(k, True, allow_not_converged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if form == "fp64":
+            th64 = th
+        out["steps"][form] = {"seconds": round(dt, 3), "iterations": int(it), "theta": float(th),
+                              "abs_dtheta_vs_fp64": None if th64 is None else abs(th - th64)}
+        print(form, out["steps"][form], flush=True)
+        dev.close()
+        torch.cuda.synchronize()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ab-initio-D", type=int, nargs="*", default=None,
                     help="one action of the K=20 active-space workload at each of these bond dimensions")
+    ap.add_argument("--ab-initio-step", type=int, nargs="*", default=None,
+                    help="one two-site step of the K=20 active-space workload at each of these bond dimensions")
+    ap.add_argument("--step-forms", nargs="*", default=["fp64", "3xtf32_tc", "fp64_tc"])
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--applies", type=int, default=3)
     ap.add_argument("--site", type=int, default=11)
@@ -95,10 +149,12 @@ def main():
     import torch
     from . import build
     build.build()
-    if args.ab_initio_D:
+    if args.ab_initio_D or args.ab_initio_step:
         import json
-        for D in args.ab_initio_D:
+        for D in args.ab_initio_D or []:
             print(json.dumps(ab_initio_action(D)), flush=True)
+        for D in args.ab_initio_step or []:
+            print(json.dumps(ab_initio_step(D, forms=tuple(args.step_forms))), flush=True)
         return
     h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune, precision=args.precision,
                               fp64_tensor_cores=args.fp64_tensor_cores)[0]
