@@ -325,6 +325,7 @@ def run_ours(args):
                      "max_abs_dE": dE, "within_1e-6": dE <= 1e-6},
         "davidson_iterations_per_sweep": {"fast": {key(h): r["iters"] for h, r in zip(hs, res_fast)},
                                           "fp64_plain": {key(h): r["iters"] for h, r in zip(hs, res_plain)}},
+        "iterations_after_fp64_switch": {"fast": {key(h): r["refine_iters"] for h, r in zip(hs, res_fast)}},
         "steps_at_iteration_cap": {"fast": {key(h): r["status"] for h, r in zip(hs, res_fast)}},
         "variants_2S=0": variants,
         "learned_correction": mlp_info,

@@ -256,8 +256,9 @@ spmps_status spmps_device_tf32_peak(int device, int kind, int sms, double* tflop
  * has no counterpart; this is an interface variant only.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its intermediates live in one
  * file-scope device array of 4 Mi doubles (32 MiB) that every GPU loading the library keeps until
- * exit; problems needing more return SPMPS_ERR_BAD_INPUT.  The H part always runs in FP64 (as
- * spmps_apply_heff with precision 0), whatever the handle's precision option.  The environments
+ * exit; problems needing more return SPMPS_ERR_BAD_INPUT.  The H part always runs FP64-accurate (as
+ * spmps_apply_heff with precision 0: on the FP64 pipe, or as split products on the tensor cores
+ * when fp64_tensor_cores is set), whatever the handle's precision option.  The environments
  * and contraction plan of `site` must already exist (a previous spmps_apply_heff or spmps_energy
  * call for that site builds them, and allocates); otherwise SPMPS_ERR_STATE.  All calls share the
  * array, which keeps the last call's contents (the call zeroes what must start at zero): calls

@@ -15,13 +15,16 @@ RTOL = 1e-10
 
 
 @pytest.mark.gpu
-def test_noalloc_apply_matches_apply_on_two_calls():
+@pytest.mark.parametrize("fp64_tc", [False, True])
+def test_noalloc_apply_matches_apply_on_two_calls(fp64_tc):
+    """Also with the FP64 block products split on the tensor cores (their status word is
+    allocated with the plan, so the call still allocates nothing)."""
     require_gpu()
     import torch
     from paper_1703_04789_gb300 import Spmps
     L, N, D, G = 8, 8, 32, 5
     labels, tens = inputs.random_mps(L, N, 0, D, 1)
-    dev = Spmps(L, N, 0, 0, G, D)
+    dev = Spmps(L, N, 0, 0, G, D, fp64_tensor_cores=fp64_tc)
     dev.set_hubbard(1.0, 4.0)
     dev.set_mps(labels, tens, center=0)
     for k in (3, 5):
