@@ -455,6 +455,93 @@ __device__ int jacobi_cta(double* A, int lda, double* V, int ldv, int n, int max
     return sweep;
 }
 
+// ---- one-warp cyclic Jacobi in FP32 --------------------------------------------------------------
+// The same round-robin pairs, rotation formula and ordering (rows, then columns) as jacobi_cta, on
+// one warp with warp-level synchronisation; A (n x n, row stride ld) symmetric, V receives the
+// rotations (eigenvectors as columns).  Used for the eigenbasis of the Ritz problem, whose lowest
+// pair is then refined in FP64.
+__device__ __forceinline__ float warp_sumf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ void jacobi_warp_f32(float* A, float* V, int ld, int n, float* cs, int* pq) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e - i * n;
+        V[i * ld + j] = i == j ? 1.0f : 0.0f;
+    }
+    __syncwarp();
+    if (n <= 1) return;
+    const int np = (n + 1) & ~1;
+    const int half = np / 2;
+    float off_prev = INFINITY;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        float off = 0.0f, tot = 0.0f;
+        for (int e = lane; e < n * n; e += 32) {
+            const int i = e / n, j = e - i * n;
+            const float v = A[i * ld + j];
+            tot += v * v;
+            if (i != j) off += v * v;
+        }
+        off = warp_sumf(off);
+        tot = warp_sumf(tot);
+        // converged to FP32 accuracy, or no longer decreasing at the rounding floor
+        if (off <= 1e-14f * tot || off == 0.0f || (off <= 1e-10f * tot && off > 0.25f * off_prev)) break;
+        off_prev = off;
+        const float tiny = 1e-10f * sqrtf(tot);
+        for (int round = 0; round < np - 1; ++round) {
+            if (lane < half) {
+                auto player = [&](int k) { return k == 0 ? 0 : 1 + ((k - 1 + round) % (np - 1)); };
+                int p = player(lane), q = player(np - 1 - lane);
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                float c = 1.0f, s = 0.0f;
+                if (q < n && fabsf(A[p * ld + q]) > tiny) {
+                    const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+                    const float theta = (aqq - app) / (2.0f * apq);
+                    const float t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+                    c = 1.0f / sqrtf(t * t + 1.0f);
+                    s = t * c;
+                } else {
+                    q = -1;
+                }
+                pq[2 * lane] = p;
+                pq[2 * lane + 1] = q;
+                cs[2 * lane] = c;
+                cs[2 * lane + 1] = s;
+            }
+            __syncwarp();
+            for (int e = lane; e < half * n; e += 32) {  // rows p, q
+                const int i = e / n, j = e - i * n;
+                const int p = pq[2 * i], q = pq[2 * i + 1];
+                if (q < 0) continue;
+                const float c = cs[2 * i], s = cs[2 * i + 1];
+                const float ap = A[p * ld + j], aq = A[q * ld + j];
+                A[p * ld + j] = c * ap - s * aq;
+                A[q * ld + j] = s * ap + c * aq;
+            }
+            __syncwarp();
+            for (int e = lane; e < half * n; e += 32) {  // columns p, q of A and V
+                const int i = e / n, j = e - i * n;
+                const int p = pq[2 * i], q = pq[2 * i + 1];
+                if (q < 0) continue;
+                const float c = cs[2 * i], s = cs[2 * i + 1];
+                const float ap = A[j * ld + p], aq = A[j * ld + q];
+                A[j * ld + p] = c * ap - s * aq;
+                A[j * ld + q] = s * ap + c * aq;
+                const float vp = V[j * ld + p], vq = V[j * ld + q];
+                V[j * ld + p] = c * vp - s * vq;
+                V[j * ld + q] = s * vp + c * vq;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 constexpr int kRitzMax = 32;
 
 // ---- incremental Ritz step --------------------------------------------------------------------
@@ -463,15 +550,16 @@ constexpr int kRitzMax = 32;
 // Adding basis vector v_m: classical Gram-Schmidt of e_m against X in the n inner product,
 // twice; the direction is kept when its n-norm^2 exceeds eps * max(diag n) (numerically null
 // directions of the metric are dropped, as in canonical orthogonalisation).  hp grows by one row
-// and column; its eigenproblem is re-solved by block-level cyclic Jacobi started from the previous
-// eigenvectors, so only the new coupling has to be rotated away.
+// and column; its eigenbasis is re-solved by one-warp FP32 Jacobi started from the previous
+// eigenvectors (so only the new coupling has to be rotated away), and the lowest pair is refined in
+// FP64 against hp (below).
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Incremental Ritz step (one CTA of 128 threads: one warp per SM sub-partition, so the FP64
-// products and the Jacobi sweeps use all four FP64 pipes of the SM).
+// Incremental Ritz step (one CTA of 128 threads: one warp per SM sub-partition for the
+// Gram-Schmidt and the products; the Jacobi sweeps and the FP64 refinement run on warp 0).
 constexpr double kMetricFloor = 1e-14;
 
 __global__ void __launch_bounds__(128) k_ritz_inc(const double* __restrict__ h, const double* __restrict__ nm, int ldm,
@@ -555,64 +643,122 @@ __global__ void __launch_bounds__(128) k_ritz_inc(const double* __restrict__ h, 
     }
     __syncthreads();
     k = k_sh;
-    // W = previous eigenvectors padded with the identity (in T), A = W^T HP W
+    // The Ritz pair.  FP32 Jacobi on W0^T HP W0, W0 = previous eigenvectors padded with the
+    // identity (so only the new row and column have to be rotated away), gives the eigenbasis W of
+    // HP to FP32 accuracy; the lowest pair is then refined in FP64 against HP itself: Rayleigh
+    // quotient y^T HP y / y^T y, residual r = HP y - theta y, and the correction
+    // sum_{j != min} w_j (w_j^T r) / (theta - lambda_j) through W's spectrum, three times, so theta
+    // and the coefficients are FP64-accurate while the O(k^3) work runs in FP32.
+    constexpr int LF = R + 1;
+    float* Af = reinterpret_cast<float*>(A);   // W0^T HP W0, then its Jacobi-diagonalised form
+    float* Vf = reinterpret_cast<float*>(T);   // HP W0, then the Jacobi rotations
+    float* W0 = reinterpret_cast<float*>(NS);  // start basis
+    float* Wf = reinterpret_cast<float*>(HS);  // eigenbasis W = W0 V
+    __shared__ float cs32[2 * R];
+    __shared__ int pq32[2 * R];
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e - i * k;
-        T[i * R + j] = (i < kc && j < kc) ? CC[i * R + j] : (i == j ? 1.0 : 0.0);
+        W0[i * LF + j] = (i < kc && j < kc) ? static_cast<float>(CC[i * R + j]) : (i == j ? 1.0f : 0.0f);
     }
     __syncthreads();
-    for (int e = tid; e < k * k; e += nt) {  // A = HP W
+    for (int e = tid; e < k * k; e += nt) {  // HP W0
         const int i = e / k, j = e - i * k;
+        float acc = 0.0f;
+        for (int l = 0; l < k; ++l) acc = fmaf(static_cast<float>(HP[i * R + l]), W0[l * LF + j], acc);
+        Vf[i * LF + j] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {  // W0^T (HP W0)
+        const int i = e / k, j = e - i * k;
+        float acc = 0.0f;
+        for (int l = 0; l < k; ++l) acc = fmaf(W0[l * LF + i], Vf[l * LF + j], acc);
+        Af[i * LF + j] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {  // symmetrise
+        const int i = e / k, j = e - i * k;
+        if (i < j) {
+            const float v = 0.5f * (Af[i * LF + j] + Af[j * LF + i]);
+            Af[i * LF + j] = v;
+            Af[j * LF + i] = v;
+        }
+    }
+    __syncthreads();
+    if (tid < 32) jacobi_warp_f32(Af, Vf, LF, k, cs32, pq32);
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {  // W = W0 V
+        const int i = e / k, j = e - i * k;
+        float acc = 0.0f;
+        for (int l = 0; l < k; ++l) acc = fmaf(W0[i * LF + l], Vf[l * LF + j], acc);
+        Wf[i * LF + j] = acc;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        // lowest diagonal entry of the rotated matrix
+        float lam = lane < k ? Af[lane * LF + lane] : INFINITY;
+        float best = lam;
+        int jmin = lane < k ? lane : R;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, jmin, o);
+            if (ob < best || (ob == best && oj < jmin)) {
+                best = ob;
+                jmin = oj;
+            }
+        }
+        double y = (lane < k && jmin < R) ? static_cast<double>(Wf[lane * LF + jmin]) : 0.0;
+        double theta = 0.0;
+        for (int it = 0; it <= 3; ++it) {
+            double hy = 0.0;
+            for (int l = 0; l < k; ++l) {
+                const double yl = __shfl_sync(0xffffffffu, y, l);
+                if (lane < k) hy = fma(HP[lane * R + l], yl, hy);
+            }
+            const double yy = warp_sum(y * y), yhy = warp_sum(y * hy);
+            theta = yy > 0.0 ? yhy / yy : 0.0;
+            if (it == 3) {
+                y = yy > 0.0 ? y / sqrt(yy) : 0.0;
+                break;
+            }
+            const double r = lane < k ? hy - theta * y : 0.0;
+            double c = 0.0;  // lane j: w_j^T r
+            for (int i = 0; i < k; ++i) {
+                const double ri = __shfl_sync(0xffffffffu, r, i);
+                if (lane < k) c = fma(static_cast<double>(Wf[i * LF + lane]), ri, c);
+            }
+            const double den = theta - static_cast<double>(lam);
+            // components (nearly) degenerate with the lowest one are left as they are
+            const bool use = lane < k && lane != jmin && fabs(den) > 1e-7 * (fabs(theta) + fabs(static_cast<double>(lam)) + 1e-300);
+            c = use ? c / den : 0.0;
+            double d = 0.0;
+            for (int j = 0; j < k; ++j) {
+                const double cj = __shfl_sync(0xffffffffu, c, j);
+                if (lane < k) d = fma(static_cast<double>(Wf[lane * LF + j]), cj, d);
+            }
+            y += d;
+        }
+        if (lane == 0) {
+            scal[0] = k > 0 ? theta : 0.0;
+            scal[1] = static_cast<double>(k);
+        }
+        // coefficients of the Ritz vector in the basis V: X y
         double acc = 0.0;
-        for (int l = 0; l < k; ++l) acc = fma(HP[i * R + l], T[l * R + j], acc);
-        A[i * R + j] = acc;
+        for (int j = 0; j < k; ++j) {
+            const double yj = __shfl_sync(0xffffffffu, y, j);
+            if (lane < m) acc = fma(X[lane + j * R], yj, acc);
+        }
+        if (lane < m) coef[lane] = k > 0 ? acc : 0.0;
     }
-    __syncthreads();
-    for (int e = tid; e < k * k; e += nt) {  // CC = W^T (HP W)  (CC is free: W holds the old C)
-        const int i = e / k, j = e - i * k;
-        double acc = 0.0;
-        for (int l = 0; l < k; ++l) acc = fma(T[l * R + i], A[l * R + j], acc);
-        CC[i * R + j] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < k * k; e += nt) {  // A = symmetrised W^T HP W
-        const int i = e / k, j = e - i * k;
-        A[i * R + j] = 0.5 * (CC[i * R + j] + CC[j * R + i]);
-    }
-    __syncthreads();
-    jacobi_cta(A, R, CC, R, k, 40, cs_sh, pq_sh, red_sh);  // CC = rotations
-    __syncthreads();
-    // new eigenvectors W * rotations, into NS (free now), then back to CC
-    for (int e = tid; e < k * k; e += nt) {
-        const int i = e / k, j = e - i * k;
-        double acc = 0.0;
-        for (int l = 0; l < k; ++l) acc = fma(T[i * R + l], CC[l * R + j], acc);
-        NS[i * R + j] = acc;
-    }
-    __syncthreads();
-    int jmin = 0;
-    for (int i = 1; i < k; ++i)
-        if (A[i * R + i] < A[jmin * R + jmin]) jmin = i;
     for (int e = tid; e < R * R; e += nt) {
         const int i = e / R, j = e - i * R;
-        const double c = (i < k && j < k) ? NS[i * R + j] : 0.0;
-        CC[e] = c;
-        st->C[e] = c;
+        st->C[e] = (i < k && j < k) ? static_cast<double>(Wf[i * LF + j]) : 0.0;
         st->X[e] = X[e];
         st->hp[e] = HP[e];
     }
-    __syncthreads();
     if (tid == 0) {
         st->k = k;
         st->m = m;
         st->kc = k;
-        scal[0] = k > 0 ? A[jmin * R + jmin] : 0.0;
-        scal[1] = static_cast<double>(k);
-    }
-    if (tid < m) {
-        double acc = 0.0;
-        for (int j = 0; j < k; ++j) acc = fma(X[tid + j * R], CC[j * R + jmin], acc);
-        coef[tid] = k > 0 ? acc : 0.0;
     }
 }
 
