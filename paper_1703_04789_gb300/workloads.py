@@ -34,6 +34,9 @@ def hubbard_chain_handles(warm_sweeps: int, spec=HUBBARD_L24, targets=None, **op
 
 
 AB_INITIO_K20 = {"K": 20, "N": 30, "twoM": 10, "twoS": 10, "n_beta": 12, "seed": 3}
+# the same integrals and electron count with M = 0 and target S = 0 (a projector that removes the
+# S = 1 .. 5 components, where the high-spin target above keeps all of M = S = 5)
+AB_INITIO_K20_S0 = {"K": 20, "N": 30, "twoM": 0, "twoS": 0, "n_beta": 12, "seed": 3}
 
 
 def ab_initio_action(D: int, spec=AB_INITIO_K20, precisions=("fp64", "3xtf32", "fp64_tc"), site=None, m_screen=0.0):
@@ -137,6 +140,7 @@ def main():
     ap.add_argument("--ab-initio-step", type=int, nargs="*", default=None,
                     help="one two-site step of the K=20 active-space workload at each of these bond dimensions")
     ap.add_argument("--step-forms", nargs="*", default=["fp64", "3xtf32_tc", "fp64_tc"])
+    ap.add_argument("--singlet", action="store_true", help="the K=20 workload with 2M = 2S = 0")
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--applies", type=int, default=3)
     ap.add_argument("--site", type=int, default=11)
@@ -151,10 +155,11 @@ def main():
     build.build()
     if args.ab_initio_D or args.ab_initio_step:
         import json
+        spec = AB_INITIO_K20_S0 if args.singlet else AB_INITIO_K20
         for D in args.ab_initio_D or []:
-            print(json.dumps(ab_initio_action(D)), flush=True)
+            print(json.dumps(ab_initio_action(D, spec=spec)), flush=True)
         for D in args.ab_initio_step or []:
-            print(json.dumps(ab_initio_step(D, forms=tuple(args.step_forms))), flush=True)
+            print(json.dumps(ab_initio_step(D, spec=spec, forms=tuple(args.step_forms))), flush=True)
         return
     h = hubbard_chain_handles(args.sweeps, targets=[[0, 0]], autotune=args.autotune, precision=args.precision,
                               fp64_tensor_cores=args.fp64_tensor_cores)[0]
