@@ -43,10 +43,10 @@ METRIC = "SP-MPS sweep time & projected H_eff·x TFLOP/s vs FP64 plain at 1e-6 E
 # Projected actions per sweep of the FP64 plain form on this workload (measured on GB300, mean of
 # the two targets); scales the oracle's per-action time to a sweep for --impl reference.
 ACTIONS_PER_PLAIN_SWEEP = 5745
-# DRAM bytes per k_gemm_oz launch of the middle-site FP64 action (phase A 74.7 MB, phase C 136.0 MB,
+# DRAM bytes per k_gemm_oz launch of the middle-site FP64 action (phase A 73.1 MB, phase C 131.2 MB,
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel, Hubbard L=24, D=256, sites
 # (11, 12) after one warm-up sweep)
-TRAFFIC_PER_LAUNCH = 105.3e6
+TRAFFIC_PER_LAUNCH = 102.2e6
 # FP16 digit products per FP64 multiply-add in the split-product GEMM (levels 2..9 of 7 x 7 digits)
 DIGIT_PRODUCTS = 34
 WORKLOAD = {
