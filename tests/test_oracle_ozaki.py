@@ -83,3 +83,37 @@ def test_random_products_within_the_bound_of_the_exact_product(seed, spread):
     assert np.all(err <= bnd)
     if spread == 0:
         assert np.all(bnd <= 4 * K * 2.0 ** -53 * (np.abs(A) @ np.abs(B)))
+
+
+def test_scheme_on_the_action_operands_stays_at_fp64_level():
+    """The two GEMM phases of the projected action (Fig. spmpsOpt) on real operands of the path --
+    rotated environments and a masked two-site vector of an L=6 Hubbard MPS at the middle site --
+    computed by the splitting scheme stay within its bound and within 1e-14 (relative to the
+    largest |A| |B| entry) of the FP64 products."""
+    from oracle import mpo as M, mps as S
+    from paper_1703_04789_gb300 import inputs
+    L, N, D, G = 6, 6, 16, 4
+    labels, tens = inputs.random_mps(L, N, 0, D, 2)
+    P = S.prepare(labels, tens, M.hubbard_mpo(L, 1.0, 4.0), 0, 0, G)
+    k = L // 2 - 1
+    P.build_left(k)
+    ql, qr = P.mps.labels[k], P.mps.labels[k + 2]
+    rng = np.random.default_rng(3)
+    x = np.where(S.two_site_mask(ql, qr), rng.standard_normal((ql.shape[0], 4, 4, qr.shape[0])), 0.0)
+    for g in range(G):
+        Lg, Rg = P.Lh[g][k], P.Rh[g][k + 2]
+        a, w, c = Lg.shape
+        A = Lg.reshape(a * w, c)                 # phase A: (a w) x c times c x (t i d)
+        B = x.reshape(c, -1)
+        T1 = Z.matmul(A, B)
+        ref = A @ B
+        scale = (np.abs(A) @ np.abs(B)).max()
+        assert np.abs(T1 - ref).max() <= 1e-14 * scale
+        # the scheme's bound plus the FP64 reference's own rounding (K u |A| |B|)
+        assert np.all(np.abs(T1 - ref) <= Z.error_bound(A, B) + c * 2.0 ** -53 * (np.abs(A) @ np.abs(B)))
+        b, u, d = Rg.shape
+        T3 = rng.standard_normal((a * 16, u * d))  # phase C: (a s j) x (u d) times (u d) x b
+        Rm = Rg.reshape(b, u * d).T
+        C = Z.matmul(T3, Rm)
+        refc = T3 @ Rm
+        assert np.abs(C - refc).max() <= 1e-14 * (np.abs(T3) @ np.abs(Rm)).max()
