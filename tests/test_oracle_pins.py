@@ -575,6 +575,23 @@ def test_mlp_features_reduce_to_diagonal_preconditioner_direction():
     assert abs(np.linalg.norm(f[:, 0]) - np.sqrt(n)) < 1e-12
 
 
+def test_mlp_features_metric_and_shifted_diagonal_columns():
+    """Columns 2 and 3 on hand-computed values: the N_eff diagonal as given, and
+    tanh((dh - theta dn) / (1 + |theta|)) with the unclamped shifted diagonal (the clamp applies only
+    to the correction of column 1): theta = -2 gives scale 3."""
+    from oracle import mlp
+    r = np.array([1.0, -1.0, 0.5])
+    dh = np.array([1.0, 0.0, -0.5])
+    dn = np.array([0.25, 0.5, 0.0])
+    f = mlp.features(r, dh, dn, -2.0)
+    assert np.array_equal(f[:, 2], dn)
+    shifted = np.array([1.0 + 0.5, 0.0 + 1.0, -0.5])  # dh - theta dn
+    assert np.allclose(f[:, 3], np.tanh(shifted / 3.0), rtol=0, atol=1e-15)
+    # a shifted diagonal of zero (dh = theta dn) maps to 0
+    g = mlp.features(np.ones(2), np.array([0.6, -0.6]), np.array([0.3, -0.3]), 2.0)
+    assert g[0, 3] == 0.0 and g[1, 3] == 0.0
+
+
 def test_adam_matches_closed_form_first_step():
     from oracle import mlp
     p = {"a": np.array([1.0, -2.0])}
