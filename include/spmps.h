@@ -95,7 +95,10 @@ typedef struct {
                            correction before it gives up with SPMPS_ERR_TIMEOUT (0 = default 2^24,
                            about a second); after giving up the kernel still waits, with the default
                            limit, for its MMAs in flight and frees its tensor memory; the same
-                           limit applies to the stacked tcgen05 GEMM of the H products */
+                           limit applies to the stacked tcgen05 GEMM of the H products and to the
+                           split-product GEMM (fp64_tensor_cores), whose give-ups the next Davidson
+                           iteration reports as SPMPS_ERR_TIMEOUT (and clears); spmps_apply_heff
+                           does not read their status word */
     int tensor_core_kernel; /* precision 1 or 2: 0 = the stacked tcgen05 GEMM (kind::tf32, operands
                            staged in shared memory, accumulator in tensor memory; tasks sharing
                            their B operand stacked along M) (default), 1 = the warp-level

@@ -390,7 +390,12 @@ spmps_status davidson_stage(spmps_t* h, int k, const double* x0, DavBuffers& B, 
         CK(cudaStreamSynchronize(h->stream));
         ++h->dav_iters;
         if (infer_err) return fail(h, SPMPS_ERR_TIMEOUT, "learned correction: a bounded tensor-core wait gave up");
-        if (tc_err) return fail(h, SPMPS_ERR_TIMEOUT, "tensor-core block GEMM: a bounded wait gave up");
+        if (tc_err) {
+            // clear the status word so that the handle stays usable after reporting
+            cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream);
+            cudaStreamSynchronize(h->stream);
+            return fail(h, SPMPS_ERR_TIMEOUT, "tensor-core block GEMM: a bounded wait gave up");
+        }
         if (host[1] < 0.5) return fail(h, SPMPS_ERR_SINGULAR_METRIC, "projected metric has no usable direction");
         if (!std::isfinite(host[0]) || !std::isfinite(host[2])) return fail(h, SPMPS_ERR_NAN, "non-finite Ritz value");
         const double theta = host[0], rn = std::sqrt(std::max(host[2], 0.0));
