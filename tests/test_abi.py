@@ -69,3 +69,17 @@ def test_no_silent_fallback_without_gpu():
     with pytest.raises(SpmpsError) as ei:
         Spmps(4, 4, 0, 0, 2, 8)
     assert ei.value.status == 6  # SPMPS_ERR_CUDA
+
+
+@pytest.mark.parametrize("field,value", [("fp64_tensor_cores", 2), ("fp64_tensor_cores", -1),
+                                         ("tensor_core_kernel", 2), ("precision", 3), ("m_screen", 1.5),
+                                         ("precond", 5)])
+def test_out_of_range_options_are_bad_input(field, value):
+    """Options outside their documented ranges are refused by spmps_create before any device work."""
+    import paper_1703_04789_gb300 as P
+    lib = P.load_library(library())
+    o = P.Options()
+    lib.spmps_default_options(C.byref(o))
+    setattr(o, field, value)
+    h = C.c_void_p()
+    assert lib.spmps_create(4, 4, 0, 0, 2, 8, C.byref(o), C.byref(h)) == 1
